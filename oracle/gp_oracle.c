@@ -1,0 +1,534 @@
+/*
+ * gp_oracle.c -- plain FP64 CPU oracle for Voxel-GPR and the covariance-centred
+ * initialisation of 3D Gaussians (GS-LIVM, arXiv 2410.17084, Sec. 3.1-3.2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The CUDA
+ * product path never links, calls or includes anything from this directory,
+ * and this file shares no code, header, table or constant generator with it.
+ *
+ * Every routine is written for a reader who checks it against the paper:
+ * textbook loops, full n x n matrices, no blocking, no fusion, no reordering
+ * beyond the definitions cited next to each function.
+ *
+ * Readings of the paper used here (each one is listed in the design doc):
+ *   - kernel: k(a,b) = sf2 * exp(-lambda * |a-b|^2) (Sec. 3.1; the paper's
+ *     setting is lambda = 1, sf2 = 1; a lengthscale l maps to 1/(2 l^2));
+ *   - noise: sigma^2 = sn2 on the Gram diagonal (Eq. 2);
+ *   - prior mean: mean_mode 1 subtracts the data mean of f and adds it back,
+ *     mean_mode 0 is the zero-mean form of Eq. 2;
+ *   - the Gram is kappa(x, x) (Alg. 1 prints kappa(x, x*) for K, which
+ *     contradicts the definition of K_alpha in Sec. 3.1);
+ *   - only the diagonal of Sigma* is produced (Sec. 3.2 uses Sigma*_i alone);
+ *   - the "eigenvector" of Sec. 3.1 is the surface normal (smallest
+ *     eigenvalue); the value axis is argmax |normal_k|, exact ties prefer
+ *     Z, then X, then Y;
+ *   - parameter axes follow Alg. 1: X -> (y, z), Y -> (z, x), Z -> (x, y);
+ *   - query grid: G = n_s * n_r cell-centred nodes per side of the voxel
+ *     face, u_i = -s/2 + (i + 1/2) s / G in voxel-local coordinates;
+ *   - weights w = 1 / max(var, 1e-6 sf2) (Eq. 6 with a floor);
+ *   - init_mode 0: scale = sqrt(max(eig, (1e-4 s)^2)) with the eigenvectors
+ *     of Phi as rotation; init_mode 1: the paper's S = diag(Phi), R = I (Eq. 8).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define GPO_OK 0
+#define GPO_BELOW_TAU 1
+#define GPO_NOT_SPD 4
+
+/* ------------------------------------------------------------------ */
+/* 3x3 symmetric eigen decomposition by cyclic Jacobi rotations.      */
+/* A is read only.  On return evals[k] is an eigenvalue and column k  */
+/* of V (V[r][k]) its unit eigenvector.  Order is not sorted.         */
+/* ------------------------------------------------------------------ */
+static void jacobi3(const double A_in[3][3], double evals[3], double V[3][3])
+{
+    double A[3][3];
+    memcpy(A, A_in, sizeof(A));
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) V[r][c] = (r == c) ? 1.0 : 0.0;
+
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        double diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+        if (off <= 1e-30 * diag || off == 0.0) break;
+        for (int p = 0; p < 2; ++p) {
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                /* rotation angle that zeroes A[p][q] */
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) /
+                           (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0);
+                double s = t * c;
+                /* A <- J^T A J with J the (p,q) plane rotation */
+                for (int k = 0; k < 3; ++k) {
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) evals[k] = A[k][k];
+}
+
+/* Exposed for the closed-form pin of the 3x3 eigen solver. */
+int gpo_eig3(const double* A9, double* evals, double* V9)
+{
+    double A[3][3], V[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) A[r][c] = A9[3 * r + c];
+    jacobi3(A, evals, V);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) V9[3 * r + c] = V[r][c];
+    return GPO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* ALG.HASH of Alg. 2: the voxel index of a point is floor(p / size)  */
+/* per coordinate, evaluated in FP32 with IEEE division (the keys are */
+/* integers, so both sides must take this decision in the same type). */
+/* ------------------------------------------------------------------ */
+void gpo_voxel_key(const float* xyz, int64_t npts, float size, int32_t* keys3)
+{
+    for (int64_t i = 0; i < npts; ++i)
+        for (int c = 0; c < 3; ++c) {
+            float q = xyz[3 * i + c] / size;
+            keys3[3 * i + c] = (int32_t)floorf(q);
+        }
+}
+
+/* Voxel centre of an integer key, in FP32: ((float)k + 0.5f) * size. */
+void gpo_voxel_centre(const int32_t* keys3, int64_t nvox, float size, float* centres)
+{
+    for (int64_t i = 0; i < 3 * nvox; ++i)
+        centres[i] = ((float)keys3[i] + 0.5f) * size;
+}
+
+/* ------------------------------------------------------------------ */
+/* ALG.PCA and the value-axis switch (Sec. 3.1, Alg. 1 switch).       */
+/* normal = eigenvector of the smallest eigenvalue of the points'     */
+/* covariance; value axis = the coordinate axis with the smallest     */
+/* angle to it = argmax |normal_k|; exact ties prefer Z, then X, Y.   */
+/* Returns the axis; also reports the normal and sorted eigenvalues.  */
+/* ------------------------------------------------------------------ */
+int gpo_pca_axis(const float* xyz, int64_t n, double* normal_out, double* evals_out)
+{
+    double c[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) c[k] += (double)xyz[3 * i + k];
+    for (int k = 0; k < 3; ++k) c[k] /= (double)n;
+
+    double C[3][3] = {{0}};
+    for (int64_t i = 0; i < n; ++i) {
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = (double)xyz[3 * i + k] - c[k];
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) C[r][s] += d[r] * d[s];
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) C[r][s] /= (double)n;
+
+    double ev[3], V[3][3];
+    jacobi3(C, ev, V);
+    int kmin = 0;
+    for (int k = 1; k < 3; ++k)
+        if (ev[k] < ev[kmin]) kmin = k;
+    double nrm[3] = {V[0][kmin], V[1][kmin], V[2][kmin]};
+
+    /* preference order Z, X, Y: a later axis wins only if strictly larger */
+    const int order[3] = {2, 0, 1};
+    int axis = order[0];
+    for (int t = 1; t < 3; ++t)
+        if (fabs(nrm[order[t]]) > fabs(nrm[axis])) axis = order[t];
+
+    if (normal_out)
+        for (int k = 0; k < 3; ++k) normal_out[k] = nrm[k];
+    if (evals_out) {
+        double s[3] = {ev[0], ev[1], ev[2]};
+        for (int a = 0; a < 3; ++a) /* sort ascending */
+            for (int b = a + 1; b < 3; ++b)
+                if (s[b] < s[a]) { double t = s[a]; s[a] = s[b]; s[b] = t; }
+        for (int k = 0; k < 3; ++k) evals_out[k] = s[k];
+    }
+    return axis;
+}
+
+/* Parameter axes of Alg. 1: X -> (y, z), Y -> (z, x), Z -> (x, y). */
+static void param_axes(int axis, int* p1, int* p2)
+{
+    *p1 = (axis + 1) % 3;
+    *p2 = (axis + 2) % 3;
+}
+
+/* Cell-centred query node i of G over a face of side s (voxel-local). */
+static double grid_node(int i, int G, double s)
+{
+    return -0.5 * s + ((double)i + 0.5) * s / (double)G;
+}
+
+/* Textbook unblocked Cholesky A = L L^T of a full n x n row-major SPD     */
+/* matrix, in place (lower triangle).  Returns 0, or -1 at a non-positive  */
+/* pivot.                                                                  */
+static int cholesky(double* A, int64_t n)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double d = A[j * n + j];
+        for (int64_t k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+        if (!(d > 0.0)) return -1;
+        double ljj = sqrt(d);
+        A[j * n + j] = ljj;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double s = A[i * n + j];
+            for (int64_t k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = s / ljj;
+        }
+    }
+    return 0;
+}
+
+/* Forward substitution L y = b (L lower, row-major full storage). */
+static void forward_sub(const double* L, int64_t n, const double* b, double* y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int64_t k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+        y[i] = s / L[i * n + i];
+    }
+}
+
+/* Back substitution L^T x = y. */
+static void backward_sub(const double* L, int64_t n, const double* y, double* x)
+{
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int64_t k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Voxel-GPR of one voxel (Alg. 1 body, Sec. 3.1 Eq. 2-3).           */
+/*                                                                    */
+/* xyz: n world points (FP32, row-major [n,3]); centre: voxel centre; */
+/* size: voxel side s; G: query nodes per side; lambda, sf2, sn2:     */
+/* kernel and noise; mean_mode as in the header; axis_override in     */
+/* {0,1,2} replaces the PCA decision (used only for axis-ambiguous    */
+/* voxels), -1 keeps it.                                              */
+/* Outputs: *axis_out, mean[G*G] (value coordinate in the voxel-local */
+/* frame) and var[G*G] = diag(Sigma*), query q = i*G + j, i on the    */
+/* first parameter axis, j on the second.                             */
+/* Returns GPO_OK or GPO_NOT_SPD.                                     */
+/* ------------------------------------------------------------------ */
+int gpo_solve_voxel(const float* xyz, int64_t n, const float* centre, double size, int G,
+                    double lambda, double sf2, double sn2, int mean_mode, int axis_override,
+                    int* axis_out, double* mean, double* var)
+{
+    int axis = axis_override >= 0 ? axis_override : gpo_pca_axis(xyz, n, NULL, NULL);
+    int p1, p2;
+    param_axes(axis, &p1, &p2);
+    *axis_out = axis;
+
+    double* x1 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* x2 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* fm = (double*)malloc(sizeof(double) * (size_t)n);
+    double* A = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    double* alpha = (double*)malloc(sizeof(double) * (size_t)n);
+    double* k = (double*)malloc(sizeof(double) * (size_t)n);
+    double* z = (double*)malloc(sizeof(double) * (size_t)n);
+
+    /* voxel-local training inputs x (parameter axes) and targets f (value axis) */
+    for (int64_t i = 0; i < n; ++i) {
+        x1[i] = (double)xyz[3 * i + p1] - (double)centre[p1];
+        x2[i] = (double)xyz[3 * i + p2] - (double)centre[p2];
+        fm[i] = (double)xyz[3 * i + axis] - (double)centre[axis];
+    }
+    double m = 0.0;
+    if (mean_mode == 1) {
+        for (int64_t i = 0; i < n; ++i) m += fm[i];
+        m /= (double)n;
+    }
+    for (int64_t i = 0; i < n; ++i) fm[i] -= m;
+
+    /* K + sigma^2 I of Eq. 2 */
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double d1 = x1[i] - x1[j], d2 = x2[i] - x2[j];
+            A[i * n + j] = sf2 * exp(-lambda * (d1 * d1 + d2 * d2)) + (i == j ? sn2 : 0.0);
+        }
+
+    int status = GPO_OK;
+    if (cholesky(A, n) != 0) {
+        status = GPO_NOT_SPD;
+        for (int q = 0; q < G * G; ++q) { mean[q] = NAN; var[q] = NAN; }
+        goto done;
+    }
+    /* alpha = (K + sigma^2 I)^-1 (f - m) */
+    forward_sub(A, n, fm, y);
+    backward_sub(A, n, y, alpha);
+
+    /* Eq. 3 at every query node: mu = m + k^T alpha, var = sf2 - |L^-1 k|^2 */
+    for (int i = 0; i < G; ++i) {
+        double u = grid_node(i, G, size);
+        for (int j = 0; j < G; ++j) {
+            double v = grid_node(j, G, size);
+            double mu = m;
+            for (int64_t t = 0; t < n; ++t) {
+                double d1 = x1[t] - u, d2 = x2[t] - v;
+                k[t] = sf2 * exp(-lambda * (d1 * d1 + d2 * d2));
+                mu += k[t] * alpha[t];
+            }
+            forward_sub(A, n, k, z);
+            double zz = 0.0;
+            for (int64_t t = 0; t < n; ++t) zz += z[t] * z[t];
+            double vv = sf2 - zz;
+            mean[i * G + j] = mu;
+            var[i * G + j] = vv > 0.0 ? vv : 0.0;
+        }
+    }
+done:
+    free(x1); free(x2); free(fm); free(A); free(y); free(alpha); free(k); free(z);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Quaternion (w, x, y, z) of a proper rotation matrix R (row-major), */
+/* the textbook trace/major-diagonal branches; sign fixed to w >= 0.  */
+/* ------------------------------------------------------------------ */
+static void quat_from_rot(const double R[3][3], double q[4])
+{
+    double tr = R[0][0] + R[1][1] + R[2][2];
+    double w, x, y, z;
+    if (tr > 0.0) {
+        double S = sqrt(tr + 1.0) * 2.0;
+        w = 0.25 * S;
+        x = (R[2][1] - R[1][2]) / S;
+        y = (R[0][2] - R[2][0]) / S;
+        z = (R[1][0] - R[0][1]) / S;
+    } else if (R[0][0] > R[1][1] && R[0][0] > R[2][2]) {
+        double S = sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]) * 2.0;
+        w = (R[2][1] - R[1][2]) / S;
+        x = 0.25 * S;
+        y = (R[0][1] + R[1][0]) / S;
+        z = (R[0][2] + R[2][0]) / S;
+    } else if (R[1][1] > R[2][2]) {
+        double S = sqrt(1.0 + R[1][1] - R[0][0] - R[2][2]) * 2.0;
+        w = (R[0][2] - R[2][0]) / S;
+        x = (R[0][1] + R[1][0]) / S;
+        y = 0.25 * S;
+        z = (R[1][2] + R[2][1]) / S;
+    } else {
+        double S = sqrt(1.0 + R[2][2] - R[0][0] - R[1][1]) * 2.0;
+        w = (R[1][0] - R[0][1]) / S;
+        x = (R[0][2] + R[2][0]) / S;
+        y = (R[1][2] + R[2][1]) / S;
+        z = 0.25 * S;
+    }
+    double nq = sqrt(w * w + x * x + y * y + z * z);
+    double sgn = (w < 0.0) ? -1.0 : 1.0;
+    q[0] = sgn * w / nq; q[1] = sgn * x / nq; q[2] = sgn * y / nq; q[3] = sgn * z / nq;
+}
+
+/* Canonical sign of an eigenvector: its largest-magnitude component is   */
+/* made positive (ties go to the lower index).                           */
+static void canon_sign(double e[3])
+{
+    int kmax = 0;
+    for (int k = 1; k < 3; ++k)
+        if (fabs(e[k]) > fabs(e[kmax])) kmax = k;
+    if (e[kmax] < 0.0)
+        for (int k = 0; k < 3; ++k) e[k] = -e[k];
+}
+
+/* ------------------------------------------------------------------ */
+/* Gaussian initialisation of one voxel (Sec. 3.2, Eq. 6-8).          */
+/*                                                                    */
+/* mean/var: the voxel's G*G GPR outputs (voxel-local value coord.);  */
+/* G = n_s * n_r; subgrid beta = (bi, bj) is the n_r x n_r block of   */
+/* query nodes starting at (bi*n_r, bj*n_r), Gaussian index           */
+/* bi*n_s + bj.  Outputs per Gaussian: pos (world, [3]), scale ([3],  */
+/* descending), quat ([4], w x y z); also the raw Phi ([9]) if given. */
+/* ------------------------------------------------------------------ */
+int gpo_init_voxel(const double* mean, const double* var, int axis, const float* centre,
+                   double size, int G, int n_s, int n_r, double sf2, int init_mode,
+                   double* pos, double* scale, double* quat, double* phi_out)
+{
+    int p1, p2;
+    if (n_r < 1 || n_r > 8 || n_s * n_r != G || axis < 0 || axis > 2) return -1;
+    param_axes(axis, &p1, &p2);
+    const double v_floor = 1e-6 * sf2;
+    const double s_floor = 1e-4 * size;
+    for (int bi = 0; bi < n_s; ++bi)
+        for (int bj = 0; bj < n_s; ++bj) {
+            int g = bi * n_s + bj;
+            double P[64][3], w[64];
+            int cnt = 0;
+            for (int ii = 0; ii < n_r; ++ii)
+                for (int jj = 0; jj < n_r; ++jj) {
+                    int i = bi * n_r + ii, j = bj * n_r + jj;
+                    int q = i * G + j;
+                    P[cnt][p1] = grid_node(i, G, size);
+                    P[cnt][p2] = grid_node(j, G, size);
+                    P[cnt][axis] = mean[q];
+                    w[cnt] = 1.0 / (var[q] > v_floor ? var[q] : v_floor);
+                    ++cnt;
+                }
+            /* Eq. 6: weighted position */
+            double sw = 0.0, p[3] = {0, 0, 0};
+            for (int t = 0; t < cnt; ++t) {
+                sw += w[t];
+                for (int k = 0; k < 3; ++k) p[k] += w[t] * P[t][k];
+            }
+            for (int k = 0; k < 3; ++k) p[k] /= sw;
+            /* Eq. 7: Phi = Q^T diag(w) Q / sum w,  Q = P - p */
+            double Phi[3][3] = {{0}};
+            for (int t = 0; t < cnt; ++t) {
+                double Q[3];
+                for (int k = 0; k < 3; ++k) Q[k] = P[t][k] - p[k];
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) Phi[r][c] += w[t] * Q[r] * Q[c];
+            }
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) Phi[r][c] /= sw;
+            if (phi_out)
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) phi_out[9 * g + 3 * r + c] = Phi[r][c];
+
+            for (int k = 0; k < 3; ++k) pos[3 * g + k] = (double)centre[k] + p[k];
+
+            if (init_mode == 1) {
+                /* Eq. 8 as printed: S = diag(Phi), R = identity quaternion */
+                for (int k = 0; k < 3; ++k) scale[3 * g + k] = Phi[k][k];
+                quat[4 * g + 0] = 1.0; quat[4 * g + 1] = 0.0;
+                quat[4 * g + 2] = 0.0; quat[4 * g + 3] = 0.0;
+                continue;
+            }
+            /* Eq. 5 read backwards: Phi = R S S^T R^T, S = sqrt(eigenvalues) */
+            double ev[3], V[3][3];
+            jacobi3(Phi, ev, V);
+            int idx[3] = {0, 1, 2};
+            for (int a = 0; a < 3; ++a) /* sort descending */
+                for (int b = a + 1; b < 3; ++b)
+                    if (ev[idx[b]] > ev[idx[a]]) { int t = idx[a]; idx[a] = idx[b]; idx[b] = t; }
+            double e1[3], e2[3], e3[3];
+            for (int k = 0; k < 3; ++k) { e1[k] = V[k][idx[0]]; e2[k] = V[k][idx[1]]; }
+            canon_sign(e1);
+            canon_sign(e2);
+            e3[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            e3[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            e3[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            double R[3][3];
+            for (int k = 0; k < 3; ++k) { R[k][0] = e1[k]; R[k][1] = e2[k]; R[k][2] = e3[k]; }
+            for (int a = 0; a < 3; ++a) {
+                double l = ev[idx[a]];
+                scale[3 * g + a] = sqrt(l > s_floor * s_floor ? l : s_floor * s_floor);
+            }
+            quat_from_rot(R, &quat[4 * g]);
+        }
+    return GPO_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Batched drivers.  Voxels are independent, so worker threads take   */
+/* one voxel at a time from a shared counter; no arithmetic changes.  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const float* xyz;
+    const int64_t* offsets;
+    int64_t nvox;
+    const float* centres;
+    const float* lambda;
+    const float* sf2;
+    const float* sn2;
+    double size;
+    int G, tau, mean_mode;
+    const int32_t* axis_override;
+    int32_t* axis;
+    double* mean;
+    double* var;
+    int32_t* status;
+    int64_t next;
+} batch_job;
+
+static void* batch_worker(void* arg)
+{
+    batch_job* J = (batch_job*)arg;
+    const int64_t GG = (int64_t)J->G * J->G;
+    for (;;) {
+        int64_t v = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (v >= J->nvox) break;
+        int64_t b = J->offsets[v], n = J->offsets[v + 1] - b;
+        double* mu = J->mean + v * GG;
+        double* va = J->var + v * GG;
+        if (n < J->tau || n <= 0) {
+            J->status[v] = GPO_BELOW_TAU;
+            J->axis[v] = -1;
+            for (int64_t q = 0; q < GG; ++q) { mu[q] = 0.0; va[q] = (double)J->sf2[v]; }
+            continue;
+        }
+        int ax = 0;
+        int ov = J->axis_override ? J->axis_override[v] : -1;
+        J->status[v] = gpo_solve_voxel(J->xyz + 3 * b, n, J->centres + 3 * v, J->size, J->G,
+                                       (double)J->lambda[v], (double)J->sf2[v],
+                                       (double)J->sn2[v], J->mean_mode, ov, &ax, mu, va);
+        J->axis[v] = ax;
+    }
+    return NULL;
+}
+
+int gpo_solve_batch(const float* xyz, const int64_t* offsets, int64_t nvox, const float* centres,
+                    const float* lambda, const float* sf2, const float* sn2, double size, int G,
+                    int tau, int mean_mode, const int32_t* axis_override, int nthreads,
+                    int32_t* axis, double* mean, double* var, int32_t* status)
+{
+    batch_job J = {xyz, offsets, nvox, centres, lambda, sf2, sn2, size, G, tau, mean_mode,
+                   axis_override, axis, mean, var, status, 0};
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, batch_worker, &J);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    return GPO_OK;
+}
+
+int gpo_init_batch(const double* mean, const double* var, const int32_t* axis,
+                   const float* centres, const float* sf2, int64_t nvox, double size, int G,
+                   int n_s, int n_r, int init_mode, double* pos, double* scale, double* quat)
+{
+    const int64_t GG = (int64_t)G * G, NG = (int64_t)n_s * n_s;
+    for (int64_t v = 0; v < nvox; ++v) {
+        if (axis[v] < 0) { /* below tau: no Gaussians are initialised */
+            for (int64_t g = 0; g < NG; ++g) {
+                for (int k = 0; k < 3; ++k) {
+                    pos[3 * (v * NG + g) + k] = (double)centres[3 * v + k];
+                    scale[3 * (v * NG + g) + k] = 0.0;
+                }
+                quat[4 * (v * NG + g) + 0] = 1.0;
+                quat[4 * (v * NG + g) + 1] = 0.0;
+                quat[4 * (v * NG + g) + 2] = 0.0;
+                quat[4 * (v * NG + g) + 3] = 0.0;
+            }
+            continue;
+        }
+        gpo_init_voxel(mean + v * GG, var + v * GG, axis[v], centres + 3 * v, size, G, n_s, n_r,
+                       (double)sf2[v], init_mode, pos + 3 * v * NG, scale + 3 * v * NG,
+                       quat + 4 * v * NG, NULL);
+    }
+    return GPO_OK;
+}
