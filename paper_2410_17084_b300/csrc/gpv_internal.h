@@ -1,0 +1,115 @@
+// gpv_internal.h -- launch arguments shared by the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpv {
+
+enum Prec { PREC_F32 = 0, PREC_FF = 1, PREC_F64 = 2 };
+
+// Per-voxel status bits (mirrors include/gp_voxels.h)
+enum : uint32_t {
+    VOX_OK = 0,
+    VOX_BELOW_TAU = 1u,
+    VOX_ESCALATED = 2u,
+    VOX_NOT_SPD = 4u,
+    VOX_TRUNCATED = 8u,
+    VOX_TOO_LARGE = 16u,
+};
+
+constexpr int kThreads = 256;   // CTA size of the solve kernels
+constexpr int kRowBlk = 8;      // rows of L^-1 per register tile
+constexpr int kQryBlk = 4;      // queries per register tile
+constexpr int kMaxG = 32;       // largest query grid side
+constexpr int kNumBuckets = 12; // size buckets of the batched launch
+
+struct SolveArgs {
+    // inputs (CSR batch of voxels)
+    const float* xyz;
+    const int64_t* offsets;
+    const float* centres;
+    const float* lam;
+    const float* sf2;
+    const float* sn2;
+    int32_t nvox;
+    float size;
+    int G, Gp, n_s, n_r, tau, mean_mode, init_mode;
+    float esc_cond;
+    int escalate;        // 1: badly conditioned voxels go to esc_list instead of being solved
+    int escalation_pass; // 1: this launch re-solves escalated voxels (sets VOX_ESCALATED)
+    // outputs
+    uint8_t* axis;
+    float* mean;
+    float* var;
+    uint32_t* status;
+    float* pos;
+    float* scale;
+    float* quat;
+    // work queue of this launch
+    const int32_t* work;
+    const int32_t* work_base;   // device: first entry of this launch in work[] (or null)
+    const int32_t* work_count;
+    int32_t* work_next;
+    int32_t* esc_list;
+    int32_t* esc_count;
+    // global-memory workspace for factors that do not fit shared memory
+    void* gws;
+    int64_t gws_stride;  // elements of the working type per CTA
+    int nmax;            // largest n handled by this launch
+    int max_points;      // voxels with more points are reported VOX_TOO_LARGE
+    int nmax_small_f64;  // escalated voxels up to this n take the shared-memory FP64 pass
+};
+
+// Shared-memory plan of one CTA (bytes), identical on host and device.
+// Elements of the working type in one CTA's global-workspace slice (factor + factors).
+__host__ __device__ inline int64_t gws_slice_elems(int nmax, int G, int Gp)
+{
+    return (int64_t)nmax * (nmax + 1) / 2 + 16 + (int64_t)nmax * G + (int64_t)nmax * Gp + 16;
+}
+
+struct SmemPlan {
+    int off_pts, off_vec, off_tri, off_a, off_b, off_part, off_mv, total;
+    int nrg, nqg;
+};
+
+__host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize, bool tri_in_smem)
+{
+    SmemPlan p;
+    int nqg = (G * Gp) / kQryBlk;
+    int nrg = nqg >= kThreads ? 1 : kThreads / nqg;
+    p.nqg = nqg;
+    p.nrg = nrg;
+    int o = 0;
+    p.off_pts = o; o = align16(o + 12 * nmax);
+    p.off_vec = o; o = align16(o + 5 * nmax * tsize);
+    p.off_tri = o;
+    // +16 elements of slack: masked tile loads near the end of the triangle stay inside
+    if (tri_in_smem) o = align16(o + (int)(((int64_t)nmax * (nmax + 1) / 2 + 16) * tsize));
+    // the cross-covariance factors live next to the triangle: in shared memory, or in
+    // the CTA's slice of the global workspace
+    p.off_a = o;
+    if (tri_in_smem) o = align16(o + nmax * G * tsize);
+    p.off_b = o;
+    if (tri_in_smem) o = align16(o + nmax * Gp * tsize);
+    p.off_part = o; o = align16(o + nrg * G * Gp * tsize);
+    p.off_mv = o; o = align16(o + 2 * G * G * 8);
+    p.total = o;
+    return p;
+}
+
+// Launchers (gpv_solve.cu)
+cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, int32_t* bcount,
+                            int32_t* bbase, int32_t* bcursor, int32_t* work, int32_t* next,
+                            int32_t* esc_count, cudaStream_t s);
+cudaError_t launch_solve(int prec, bool tri_in_smem, const SolveArgs& a, int grid, int smem,
+                         cudaStream_t s);
+cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out);
+cudaError_t solve_occupancy(int prec, bool tri_in_smem, int smem, int* blocks_per_sm);
+cudaError_t launch_init(const float* mean, const float* var, const uint8_t* axis,
+                        const float* centres, const float* sf2, const uint32_t* status,
+                        int32_t nvox, float size, int G, int n_s, int n_r, int init_mode,
+                        float* pos, float* scale, float* quat, cudaStream_t s);
+
+}  // namespace gpv

@@ -1,0 +1,619 @@
+// gpv_solve.cu -- batched Voxel-GPR (GS-LIVM Sec. 3.1, Alg. 1, Eq. 2-3) on sm_103a.
+//
+// One CTA solves one voxel at a time and pulls the next voxel from a per-launch work
+// queue (a persistent grid sized to the SM count).  Per voxel, all in shared memory:
+//   A1  PCA of the points (FP64 sums, 3x3 Jacobi) -> value axis (Sec. 3.1)
+//   A2  voxel-local training inputs x (parameter axes) and targets f (value axis)
+//   A3  Gram K + sigma^2 I, packed lower triangle, column-major (Eq. 2)
+//   A4  Cholesky K + sigma^2 I = L L^T, right-looking, one barrier per column
+//       (replaces the LU + explicit inverse of the paper's Alg. 3)
+//       -> L^-1 in place (n^3/6 more flops buys a barrier-free contraction below)
+//   A5  alpha = L^-T L^-1 (f - m)
+//   A6  K* on the G x G query grid is separable: k(x_i, (u,v)) = a_i(u) b_i(v), so
+//       only 2 n G exponentials are evaluated
+//   A7  mu* = m + K*^T alpha (Eq. 3)
+//   A8  diag(Sigma*) = sf2 - |L^-1 k_q|^2: a dense contraction L^-1 * K* tiled 8 rows
+//       x 4 queries per thread, squared and summed on the fly; the n x G^2 matrix
+//       L^-1 K* and the full Sigma* of Alg. 3 are never formed
+//   A10 (optional, fused) Gaussian initialisation of the n_s^2 subgrids (Sec. 3.2)
+// The same code is instantiated for float, double and float-float ("ff").
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gpv_init.cuh"
+#include "gpv_internal.h"
+#include "gpv_num.cuh"
+
+namespace gpv {
+
+// column-major packed lower triangle of an n x n matrix: element (r, c), r >= c
+__device__ __forceinline__ int tri_off(int c, int n) { return c * n - ((c * (c - 1)) >> 1); }
+
+__device__ __forceinline__ float shfl_x(float x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+__device__ __forceinline__ double shfl_x(double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+__device__ __forceinline__ ff shfl_x(ff x, int o)
+{
+    return ff_make(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
+}
+
+// Sum of K values of type R over the CTA (fixed order: deterministic); every thread
+// gets the totals.  red must hold K * 32 values of R.
+template <class R, int K>
+__device__ __forceinline__ void block_sum(R (&v)[K], R* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] = v[k] + shfl_x(v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * 32 + wid] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        R s = red[k * 32];
+        for (int w = 1; w < nw; ++w) s = s + red[k * 32 + w];
+        v[k] = s;
+    }
+    __syncthreads();
+}
+
+// Value axis of a point set: normal = eigenvector of the smallest eigenvalue of the
+// covariance; axis = argmax |normal_k| with exact ties resolved Z, then X, then Y.
+// The decision needs no more than FP32: voxels whose two largest normal components
+// lie within 1e-3 are axis-ambiguous by definition.
+__device__ inline int value_axis_from_cov(const float c6[6])
+{
+    float ev[3], E[9];
+    sym3_eig<float>(c6, ev, E);
+    int k = 0;
+    if (ev[1] < ev[k]) k = 1;
+    if (ev[2] < ev[k]) k = 2;
+    const float nx = fabsf(E[0 + k]), ny = fabsf(E[3 + k]), nz = fabsf(E[6 + k]);
+    int ax = 2;
+    float best = nz;
+    if (nx > best) { ax = 0; best = nx; }
+    if (ny > best) { ax = 1; }
+    return ax;
+}
+
+template <class T, bool TRI_SMEM>
+__device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, const SmemPlan& P,
+                            double* red, const T* nodes)
+{
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    const int64_t beg = A.offsets[v];
+    const int n = (int)(A.offsets[v + 1] - beg);
+    const int G = A.G, Gp = A.Gp, GG = G * G;
+
+    float* pts = reinterpret_cast<float*>(smem + P.off_pts);
+    T* x1 = reinterpret_cast<T*>(smem + P.off_vec);
+    T* x2 = x1 + A.nmax;
+    T* fv = x2 + A.nmax;
+    T* al = fv + A.nmax;
+    T* tmp = al + A.nmax;
+    T* L = TRI_SMEM ? reinterpret_cast<T*>(smem + P.off_tri)
+                    : reinterpret_cast<T*>(A.gws) + (int64_t)blockIdx.x * A.gws_stride;
+    T* fa = TRI_SMEM ? reinterpret_cast<T*>(smem + P.off_a)
+                     : L + ((int64_t)A.nmax * (A.nmax + 1) / 2 + 16);
+    T* fb = TRI_SMEM ? reinterpret_cast<T*>(smem + P.off_b) : fa + (int64_t)A.nmax * G;
+    T* part = reinterpret_cast<T*>(smem + P.off_part);
+    T* mv = reinterpret_cast<T*>(smem + P.off_mv);
+    __shared__ int s_axis;
+    __shared__ int s_fail;
+
+    // ---- load points (3n contiguous floats) ------------------------------------
+    const float* src = A.xyz + 3 * beg;
+    for (int t = tid; t < 3 * n; t += nthr) pts[t] = __ldg(src + t);
+    __syncthreads();
+
+    // ---- A1: PCA (FP32, voxel-local coordinates) -> value axis --------------------
+    const float cx = A.centres[3 * v + 0], cy = A.centres[3 * v + 1], cz = A.centres[3 * v + 2];
+    {
+        float* redf = reinterpret_cast<float*>(red);
+        float s3[3] = {0.f, 0.f, 0.f};
+        for (int i = tid; i < n; i += nthr) {
+            s3[0] += pts[3 * i + 0] - cx;
+            s3[1] += pts[3 * i + 1] - cy;
+            s3[2] += pts[3 * i + 2] - cz;
+        }
+        block_sum<float, 3>(s3, redf);
+        const float inv_n = 1.f / (float)n;
+        const float m0 = s3[0] * inv_n, m1 = s3[1] * inv_n, m2 = s3[2] * inv_n;
+        float c6[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = tid; i < n; i += nthr) {
+            const float d0 = (pts[3 * i + 0] - cx) - m0;
+            const float d1 = (pts[3 * i + 1] - cy) - m1;
+            const float d2 = (pts[3 * i + 2] - cz) - m2;
+            c6[0] += d0 * d0; c6[1] += d0 * d1; c6[2] += d0 * d2;
+            c6[3] += d1 * d1; c6[4] += d1 * d2; c6[5] += d2 * d2;
+        }
+        block_sum<float, 6>(c6, redf);
+        if (tid == 0) {
+            s_axis = value_axis_from_cov(c6);
+            s_fail = 0;
+        }
+        __syncthreads();
+    }
+    const int axis = s_axis;
+    const int p1 = axis == 2 ? 0 : axis + 1;
+    const int p2 = axis == 0 ? 2 : (axis == 1 ? 0 : 1);
+    const float cen[3] = {cx, cy, cz};
+
+    // ---- A2: voxel-local inputs and targets, prior mean ---------------------------
+    T msum[1] = {zero<T>()};
+    for (int i = tid; i < n; i += nthr) {
+        x1[i] = diff_f<T>(pts[3 * i + p1], cen[p1]);
+        x2[i] = diff_f<T>(pts[3 * i + p2], cen[p2]);
+        T f = diff_f<T>(pts[3 * i + axis], cen[axis]);
+        fv[i] = f;
+        msum[0] = msum[0] + f;
+    }
+    block_sum<T, 1>(msum, reinterpret_cast<T*>(red));
+    const T m = A.mean_mode == 1 ? msum[0] / from_f<T>((float)n) : zero<T>();
+    for (int i = tid; i < n; i += nthr) fv[i] = fv[i] - m;
+
+    // ---- A3: Gram + noise (packed lower, column-major) ---------------------------
+    const float lamf = A.lam[v], sf2f = A.sf2[v], sn2f = A.sn2[v];
+    const T nlam = from_f<T>(-lamf);
+    const T sf2 = from_f<T>(sf2f);
+    const T sn2 = from_f<T>(sn2f);
+    __syncthreads();
+    {
+        // column c, rows r = c..n-1; one warp per column, lanes over rows
+        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+        for (int c = wid; c < n; c += nw) {
+            const T xc = x1[c], yc = x2[c];
+            T* col = L + tri_off(c, n);
+            for (int r = c + lane; r < n; r += 32) {
+                T d1 = x1[r] - xc, d2 = x2[r] - yc;
+                T k = sf2 * gexp(nlam * (d1 * d1 + d2 * d2));
+                if (r == c) k = k + sn2;
+                col[r - c] = k;
+            }
+        }
+    }
+
+    // ---- A4: Cholesky, right-looking, unscaled trailing update ---------------------
+    // step k: A_ij -= A_ik A_jk / A_kk for k < j <= i, column k-1 scaled in the same
+    // phase (it is not read by step k), one barrier per step.
+    float dmin = 3.0e38f, dmax = 0.f;
+    {
+        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+        T dprev = zero<T>();
+        T rs_prev = zero<T>();
+        for (int k = 0; k < n; ++k) {
+            __syncthreads();
+            const T d = L[tri_off(k, n)];
+            const float dh = hi_of(d);
+            if (!(dh > 0.f)) {
+                if (tid == 0) s_fail = 1;
+                break;
+            }
+            dmin = fminf(dmin, dh);
+            dmax = fmaxf(dmax, dh);
+            if (k > 0) {  // finish column k-1
+                T* ck = L + tri_off(k - 1, n);
+                for (int r = tid; r < n - (k - 1); r += nthr)
+                    ck[r] = (r == 0) ? gsqrt(dprev) : ck[r] * rs_prev;
+            }
+            const T inv_d = from_f<T>(1.f) / d;
+            const T* colk = L + tri_off(k, n);
+            for (int j = k + 1 + wid; j < n; j += nw) {
+                const T s = colk[j - k] * inv_d;
+                T* colj = L + tri_off(j, n);
+                for (int i = j + lane; i < n; i += 32) colj[i - j] = gfnma(colk[i - k], s, colj[i - j]);
+            }
+            dprev = d;
+            rs_prev = from_f<T>(1.f) / gsqrt(d);
+        }
+        __syncthreads();
+        if (!s_fail && tid == 0) L[tri_off(n - 1, n)] = gsqrt(dprev);
+        __syncthreads();
+    }
+    const bool ill = s_fail || (dmax > A.esc_cond * dmin);
+    if (ill && A.escalate) {
+        if (tid == 0) {
+            const int big = n > A.nmax_small_f64 ? 1 : 0;
+            int slot = atomicAdd(A.esc_count + big, 1);
+            A.esc_list[(int64_t)big * A.nvox + slot] = v;
+        }
+        __syncthreads();
+        return;
+    }
+    const int64_t obase = (int64_t)v * GG;
+    if (s_fail) {
+        // not positive definite in this precision: report the prior
+        for (int q = tid; q < GG; q += nthr) {
+            A.mean[obase + q] = to_f(m);
+            A.var[obase + q] = sf2f;
+        }
+        if (tid == 0) {
+            A.axis[v] = (uint8_t)axis;
+            A.status[v] = VOX_NOT_SPD | (A.escalation_pass ? VOX_ESCALATED : 0u);
+        }
+        if (A.pos) {
+            const int NG = A.n_s * A.n_s;
+            for (int g = tid; g < NG; g += nthr) {
+                const int64_t o = (int64_t)v * NG + g;
+                for (int k = 0; k < 3; ++k) { A.pos[3 * o + k] = cen[k]; A.scale[3 * o + k] = 0.f; }
+                A.quat[4 * o] = 1.f; A.quat[4 * o + 1] = 0.f; A.quat[4 * o + 2] = 0.f; A.quat[4 * o + 3] = 0.f;
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    // ---- A4': X = L^-1 in place, right-looking elimination of L X = I -------------
+    // step k: (a) row k is final: X_kc = B_kc / L_kk (c < k);
+    //         (b) rows i > k: B_ic -= L_ik X_kc (c < k) and B_ik = -L_ik / L_kk.
+    // B_ic overwrites L_ic (c < k, consumed at step c).  One warp owns row i in (b), so
+    // it reads L_ik before the lane of column k overwrites it.  The diagonal keeps L_kk
+    // until a last pass writes 1 / L_kk.  Two barriers per step; no thread runs a
+    // serial dot product.
+    {
+        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+        for (int k = 0; k < n; ++k) {
+            __syncthreads();
+            const T inv = from_f<T>(1.f) / L[tri_off(k, n)];
+            for (int c = tid; c < k; c += nthr) {
+                T* p = L + tri_off(c, n) + (k - c);
+                *p = (*p) * inv;
+            }
+            __syncthreads();
+            for (int i = k + 1 + wid; i < n; i += nw) {
+                const T m = L[tri_off(k, n) + (i - k)];
+                __syncwarp();
+                for (int c = lane; c <= k; c += 32) {
+                    T* p = L + tri_off(c, n) + (i - c);
+                    *p = (c == k) ? -(m * inv) : gfnma(m, L[tri_off(c, n) + (k - c)], *p);
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = tid; k < n; k += nthr) {
+            T* p = L + tri_off(k, n);
+            *p = from_f<T>(1.f) / (*p);
+        }
+        __syncthreads();
+    }
+
+    // ---- A5: alpha = X^T (X (f - m)) ----------------------------------------------
+    for (int j = tid; j < n; j += nthr) {
+        T s = zero<T>();
+        for (int i = 0; i <= j; ++i) s = gfma(L[tri_off(i, n) + (j - i)], fv[i], s);
+        tmp[j] = s;
+    }
+    // ---- A6: separable cross-covariance factors --------------------------------------
+    {
+        for (int t = tid; t < n * G; t += nthr) {
+            const int i = t / G, u = t - i * G;
+            const T node = nodes[u];
+            T d1 = x1[i] - node;
+            T d2 = x2[i] - node;
+            fa[i * G + u] = sf2 * gexp(nlam * (d1 * d1));
+            fb[i * Gp + u] = gexp(nlam * (d2 * d2));
+        }
+        for (int t = tid; t < n * (Gp - G); t += nthr) {
+            const int i = t / (Gp - G), u = G + (t - i * (Gp - G));
+            fb[i * Gp + u] = zero<T>();
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nthr) {
+        T s = zero<T>();
+        for (int j = i; j < n; ++j) s = gfma(L[tri_off(i, n) + (j - i)], tmp[j], s);
+        al[i] = s;
+    }
+
+    // ---- A8: |X k_q|^2 by register-tiled contraction ------------------------------
+    {
+        const int nqg = P.nqg, nrg = P.nrg;
+        const int nb = (n + kRowBlk - 1) / kRowBlk;
+        for (int w = tid; w < nqg * nrg; w += nthr) {
+            const int qg = w % nqg, rg = w / nqg;
+            const int q0 = qg * kQryBlk;
+            const int u = q0 / Gp, v0 = q0 - u * Gp;
+            T nrm[kQryBlk];
+#pragma unroll
+            for (int r = 0; r < kQryBlk; ++r) nrm[r] = zero<T>();
+            // snake assignment of row blocks to row groups balances the triangle
+            for (int s = 0;; ++s) {
+                const int jb = (s & 1) ? (s + 1) * nrg - 1 - rg : s * nrg + rg;
+                if (s * nrg >= nb) break;
+                if (jb >= nb) continue;
+                const int j0 = jb * kRowBlk;
+                const int nrow = min(kRowBlk, n - j0);
+                T acc[kRowBlk][kQryBlk];
+#pragma unroll
+                for (int a = 0; a < kRowBlk; ++a)
+#pragma unroll
+                    for (int r = 0; r < kQryBlk; ++r) acc[a][r] = zero<T>();
+                const int iend = min(j0 + kRowBlk, n);
+                for (int i = 0; i < iend; ++i) {
+                    const T ai = fa[i * G + u];
+                    T kq[kQryBlk];
+#pragma unroll
+                    for (int r = 0; r < kQryBlk; ++r) kq[r] = ai * fb[i * Gp + v0 + r];
+                    const T* col = L + tri_off(i, n) + (j0 - i);
+#pragma unroll
+                    for (int a = 0; a < kRowBlk; ++a) {
+                        // rows j0+a of column i; zero above the diagonal and past n
+                        const bool ok = (a < nrow) && (j0 + a >= i);
+                        const T l = ok ? col[a] : zero<T>();
+#pragma unroll
+                        for (int r = 0; r < kQryBlk; ++r) acc_fma(acc[a][r], l, kq[r]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < kRowBlk; ++a)
+#pragma unroll
+                    for (int r = 0; r < kQryBlk; ++r) {
+                        const T x = acc_norm(acc[a][r]);
+                        nrm[r] = gfma(x, x, nrm[r]);
+                    }
+            }
+#pragma unroll
+            for (int r = 0; r < kQryBlk; ++r) part[rg * (G * Gp) + q0 + r] = nrm[r];
+        }
+    }
+    __syncthreads();
+
+    // ---- A7 + A8 epilogue: mean and variance per query ----------------------------
+    const bool want_init = A.pos != nullptr;
+    for (int q = tid; q < GG; q += nthr) {
+        const int u = q / G, vv = q - u * G;
+        T mu = m;
+        for (int i = 0; i < n; ++i) mu = gfma(al[i] * fa[i * G + u], fb[i * Gp + vv], mu);
+        T nr = zero<T>();
+        for (int g = 0; g < P.nrg; ++g) nr = nr + part[g * (G * Gp) + u * Gp + vv];
+        T var = sf2 - nr;
+        if (!(hi_of(var) > 0.f)) var = zero<T>();
+        A.mean[obase + q] = to_f(mu);
+        A.var[obase + q] = to_f(var);
+        if (want_init) { mv[q] = mu; mv[GG + q] = var; }
+    }
+    if (tid == 0) {
+        A.axis[v] = (uint8_t)axis;
+        uint32_t st = A.escalation_pass ? VOX_ESCALATED : 0u;
+        A.status[v] = st;
+    }
+    // ---- A10 (fused): Gaussians of the n_s x n_s subgrids ---------------------------
+    if (want_init) {
+        __syncthreads();
+        const int NG = A.n_s * A.n_s;
+        for (int g = tid; g < NG; g += nthr) {
+            const int64_t o = (int64_t)v * NG + g;
+            init_one_gaussian<T>(mv, mv + GG, nodes, axis, cen, A.size, G, A.n_s, A.n_r, sf2f,
+                                 A.init_mode, g / A.n_s, g % A.n_s, A.pos + 3 * o,
+                                 A.scale + 3 * o, A.quat + 4 * o);
+        }
+    }
+    __syncthreads();
+}
+
+template <class T, bool TRI_SMEM>
+__global__ void __launch_bounds__(kThreads) k_solve(SolveArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[6 * 32];
+    __shared__ T nodes[kMaxG];
+    __shared__ int s_v;
+    const SmemPlan P = smem_plan(A.nmax, A.G, A.Gp, (int)sizeof(T), TRI_SMEM);
+    // query grid nodes -s/2 + (u + 1/2) s / G, formed once in FP64 and rounded to T
+    if (threadIdx.x < A.G)
+        nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
+                                       ((double)threadIdx.x + 0.5) * (double)A.size / (double)A.G);
+    const int total = *A.work_count;
+    const int base = A.work_base ? *A.work_base : 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int i = atomicAdd(A.work_next, 1);
+            s_v = i < total ? A.work[base + i] : -1;
+        }
+        __syncthreads();
+        const int v = s_v;
+        __syncthreads();
+        if (v < 0) break;
+        solve_voxel<T, TRI_SMEM>(A, v, smem, P, red, nodes);
+    }
+}
+
+// ---- size classification into buckets (device-side, no host round trip) -------
+__global__ void k_classify(SolveArgs A, const int* bucket_hi, int nb, int32_t* bcount)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= A.nvox) return;
+    const int64_t n = A.offsets[v + 1] - A.offsets[v];
+    if (n < A.tau || n <= 0 || n > A.max_points) {
+        const int GG = A.G * A.G;
+        const float sf2 = A.sf2[v];
+        for (int q = 0; q < GG; ++q) {
+            A.mean[(int64_t)v * GG + q] = 0.f;
+            A.var[(int64_t)v * GG + q] = sf2;
+        }
+        A.axis[v] = 255;
+        A.status[v] = n > A.max_points ? VOX_TOO_LARGE : VOX_BELOW_TAU;
+        if (A.pos) {
+            const int NG = A.n_s * A.n_s;
+            for (int g = 0; g < NG; ++g) {
+                const int64_t o = (int64_t)v * NG + g;
+                for (int k = 0; k < 3; ++k) {
+                    A.pos[3 * o + k] = A.centres[3 * v + k];
+                    A.scale[3 * o + k] = 0.f;
+                }
+                A.quat[4 * o] = 1.f; A.quat[4 * o + 1] = 0.f; A.quat[4 * o + 2] = 0.f; A.quat[4 * o + 3] = 0.f;
+            }
+        }
+        return;
+    }
+    int b = nb - 1;
+    for (int k = 0; k < nb; ++k)
+        if (n <= bucket_hi[k]) { b = k; break; }
+    atomicAdd(&bcount[b], 1);
+}
+
+__global__ void k_scan(int nb, const int32_t* bcount, int32_t* bbase, int32_t* bcursor,
+                       int32_t* next, int32_t* esc_count)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int s = 0;
+    for (int b = 0; b < nb; ++b) {
+        bbase[b] = s;
+        bcursor[b] = 0;
+        next[b] = 0;
+        s += bcount[b];
+    }
+    next[nb] = 0;  // dequeue counters of the two escalation passes
+    next[nb + 1] = 0;
+    esc_count[0] = 0;
+    esc_count[1] = 0;
+}
+
+__global__ void k_scatter(SolveArgs A, const int* bucket_hi, int nb, const int32_t* bbase,
+                          int32_t* bcursor, int32_t* work)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= A.nvox) return;
+    const int64_t n = A.offsets[v + 1] - A.offsets[v];
+    if (n < A.tau || n <= 0 || n > A.max_points) return;
+    int b = nb - 1;
+    for (int k = 0; k < nb; ++k)
+        if (n <= bucket_hi[k]) { b = k; break; }
+    const int slot = atomicAdd(&bcursor[b], 1);
+    work[bbase[b] + slot] = v;
+}
+
+cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, int32_t* bcount,
+                            int32_t* bbase, int32_t* bcursor, int32_t* work, int32_t* next,
+                            int32_t* esc_count, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bcount, 0, sizeof(int32_t) * nb, s);
+    if (e != cudaSuccess) return e;
+    if (a.nvox > 0) {
+        const int blk = 256, grd = (a.nvox + blk - 1) / blk;
+        k_classify<<<grd, blk, 0, s>>>(a, bucket_hi, nb, bcount);
+    }
+    k_scan<<<1, 32, 0, s>>>(nb, bcount, bbase, bcursor, next, esc_count);
+    if (a.nvox > 0) {
+        const int blk = 256, grd = (a.nvox + blk - 1) / blk;
+        k_scatter<<<grd, blk, 0, s>>>(a, bucket_hi, nb, bbase, bcursor, work);
+    }
+    return cudaGetLastError();
+}
+
+// The dynamic shared-memory limit of every instantiation is raised once, when the
+// handle plans its launches (solve_occupancy), so launches stay capturable.
+template <class T, bool S>
+static cudaError_t launch_t(const SolveArgs& a, int grid, int smem, cudaStream_t s)
+{
+    k_solve<T, S><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(int prec, bool tri_in_smem, const SolveArgs& a, int grid, int smem,
+                         cudaStream_t s)
+{
+    if (prec == PREC_F32) return tri_in_smem ? launch_t<float, true>(a, grid, smem, s) : launch_t<float, false>(a, grid, smem, s);
+    if (prec == PREC_F64) return tri_in_smem ? launch_t<double, true>(a, grid, smem, s) : launch_t<double, false>(a, grid, smem, s);
+    return tri_in_smem ? launch_t<ff, true>(a, grid, smem, s) : launch_t<ff, false>(a, grid, smem, s);
+}
+
+static int tsize_of(int prec) { return prec == PREC_F32 ? 4 : 8; }
+
+cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int static_bytes = 6 * 32 * 8 + 64;
+    int best = 0;
+    for (int n = 8; n <= 1024; n += 8) {
+        SmemPlan p = smem_plan(n, G, Gp, tsize_of(prec), true);
+        if (p.total + static_bytes <= optin) best = n;
+    }
+    *nmax_out = best;
+    return cudaSuccess;
+}
+
+cudaError_t solve_occupancy(int prec, bool tri_in_smem, int smem, int* blocks_per_sm)
+{
+    const void* f;
+    if (prec == PREC_F32) f = tri_in_smem ? (const void*)k_solve<float, true> : (const void*)k_solve<float, false>;
+    else if (prec == PREC_F64) f = tri_in_smem ? (const void*)k_solve<double, true> : (const void*)k_solve<double, false>;
+    else f = tri_in_smem ? (const void*)k_solve<ff, true> : (const void*)k_solve<ff, false>;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    if (smem > optin - (int)fa.sharedSizeBytes) { *blocks_per_sm = 0; return cudaSuccess; }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
+}
+
+// ---- standalone Gaussian initialisation from FP32 predictions ---------------------
+__global__ void k_init(const float* mean, const float* var, const uint8_t* axis,
+                       const float* centres, const float* sf2, const uint32_t* status,
+                       int32_t nvox, float size, int G, int n_s, int n_r, int init_mode,
+                       float* pos, float* scale, float* quat)
+{
+    extern __shared__ ff mvs[];  // per warp: 2 G^2 values
+    __shared__ ff nodes[kMaxG];
+    if (threadIdx.x < G)
+        nodes[threadIdx.x] = from_d<ff>(-0.5 * (double)size +
+                                        ((double)threadIdx.x + 0.5) * (double)size / (double)G);
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const int v = blockIdx.x * nw + wid;
+    if (v >= nvox) return;
+    const int GG = G * G, NG = n_s * n_s;
+    ff* mv = mvs + (size_t)wid * 2 * GG;
+    for (int q = lane; q < GG; q += 32) {
+        mv[q] = from_f<ff>(mean[(int64_t)v * GG + q]);
+        mv[GG + q] = from_f<ff>(var[(int64_t)v * GG + q]);
+    }
+    __syncwarp();
+    const bool skip = (status && (status[v] & (VOX_BELOW_TAU | VOX_NOT_SPD | VOX_TOO_LARGE))) ||
+                      axis[v] > 2;
+    for (int g = lane; g < NG; g += 32) {
+        const int64_t o = (int64_t)v * NG + g;
+        if (skip) {
+            for (int k = 0; k < 3; ++k) { pos[3 * o + k] = centres[3 * v + k]; scale[3 * o + k] = 0.f; }
+            quat[4 * o] = 1.f; quat[4 * o + 1] = 0.f; quat[4 * o + 2] = 0.f; quat[4 * o + 3] = 0.f;
+            continue;
+        }
+        init_one_gaussian<ff>(mv, mv + GG, nodes, axis[v], centres + 3 * v, size, G, n_s, n_r,
+                              sf2[v], init_mode, g / n_s, g % n_s, pos + 3 * o, scale + 3 * o,
+                              quat + 4 * o);
+    }
+}
+
+cudaError_t launch_init(const float* mean, const float* var, const uint8_t* axis,
+                        const float* centres, const float* sf2, const uint32_t* status,
+                        int32_t nvox, float size, int G, int n_s, int n_r, int init_mode,
+                        float* pos, float* scale, float* quat, cudaStream_t s)
+{
+    if (nvox <= 0) return cudaSuccess;
+    // one warp per voxel, its G^2 predictions staged as float-float; stay under 48 KB
+    const int per_warp = 2 * G * G * (int)sizeof(ff);
+    const int warps = per_warp * 4 <= 48 * 1024 ? 4 : (per_warp * 2 <= 48 * 1024 ? 2 : 1);
+    const int smem = warps * per_warp;
+    const int grid = (nvox + warps - 1) / warps;
+    k_init<<<grid, warps * 32, smem, s>>>(mean, var, axis, centres, sf2, status, nvox, size, G,
+                                          n_s, n_r, init_mode, pos, scale, quat);
+    return cudaGetLastError();
+}
+
+}  // namespace gpv

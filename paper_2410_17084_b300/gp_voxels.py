@@ -1,0 +1,224 @@
+"""Thin ctypes binding of ``include/gp_voxels.h`` (libgp_voxels.so, sm_103a).
+
+Argument marshalling only: every step of the Voxel-GPR path runs in the CUDA
+library.  PyTorch supplies device memory (``tensor.data_ptr()``) and streams
+(``torch.cuda.current_stream().cuda_stream``).  If the library is missing, importing
+the functions raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgp_voxels.so")
+
+GPV_OK, GPV_EINVAL, GPV_ENOMEM, GPV_EBUDGET, GPV_ECUDA, GPV_ETIMEOUT, GPV_EFULL = 0, -1, -2, -3, -4, -5, -6
+VOX_OK, VOX_BELOW_TAU, VOX_ESCALATED, VOX_NOT_SPD, VOX_TRUNCATED, VOX_TOO_LARGE = 0, 1, 2, 4, 8, 16
+PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
+SOLVE_ONE_PER_LAUNCH = 1
+
+EXPORTED = [
+    "gp_voxels_config_default", "gp_voxels_create", "gp_voxels_destroy", "gp_voxels_solve_csr",
+    "gp_voxels_init_gaussians", "gp_voxels_query_sizes", "gp_voxels_strerror",
+    "gp_voxels_last_error",
+]
+
+
+class gp_voxels_config(ctypes.Structure):
+    _fields_ = [
+        ("voxel_size", ctypes.c_float),
+        ("grid_side", ctypes.c_int),
+        ("n_s", ctypes.c_int),
+        ("n_r", ctypes.c_int),
+        ("tau", ctypes.c_int),
+        ("max_points", ctypes.c_int),
+        ("max_voxels", ctypes.c_int),
+        ("mean_mode", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("init_mode", ctypes.c_int),
+        ("esc_cond", ctypes.c_float),
+        ("hash_capacity", ctypes.c_uint32),
+        ("mem_budget", ctypes.c_size_t),
+    ]
+
+
+class GpvError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__(f"{fn} failed: {strerror(code)} ({code}) {last_error()}")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgp_voxels.so; raises if it was not built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2410_17084_b300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32
+        L.gp_voxels_config_default.argtypes = [ctypes.POINTER(gp_voxels_config)]
+        L.gp_voxels_create.argtypes = [ctypes.POINTER(gp_voxels_config), ctypes.POINTER(P)]
+        L.gp_voxels_destroy.argtypes = [P]
+        L.gp_voxels_solve_csr.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P, P, P, P, P, P,
+                                          P, U32, P]
+        L.gp_voxels_init_gaussians.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P, P, P, P]
+        L.gp_voxels_query_sizes.argtypes = [ctypes.POINTER(gp_voxels_config),
+                                            ctypes.POINTER(ctypes.c_size_t)]
+        L.gp_voxels_strerror.argtypes = [I]
+        L.gp_voxels_strerror.restype = ctypes.c_char_p
+        L.gp_voxels_last_error.argtypes = []
+        L.gp_voxels_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("gp_voxels_strerror", "gp_voxels_last_error"):
+                getattr(L, name).restype = I
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().gp_voxels_strerror(int(code)).decode()
+
+
+def last_error() -> str:
+    return lib().gp_voxels_last_error().decode()
+
+
+def _check(fn, rc):
+    if rc != GPV_OK:
+        raise GpvError(fn, rc)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---- same names as the C ABI -----------------------------------------------------
+def gp_voxels_config_default(**overrides) -> gp_voxels_config:
+    cfg = gp_voxels_config()
+    _check("gp_voxels_config_default", lib().gp_voxels_config_default(ctypes.byref(cfg)))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def gp_voxels_create(cfg: gp_voxels_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check("gp_voxels_create", lib().gp_voxels_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def gp_voxels_destroy(h) -> None:
+    _check("gp_voxels_destroy", lib().gp_voxels_destroy(h))
+
+
+def gp_voxels_query_sizes(cfg: gp_voxels_config) -> int:
+    n = ctypes.c_size_t()
+    _check("gp_voxels_query_sizes", lib().gp_voxels_query_sizes(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def gp_voxels_solve_csr(h, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, mean, var, status,
+                        pos=None, scale=None, quat=None, flags=0, stream=None) -> None:
+    rc = lib().gp_voxels_solve_csr(h, _ptr(xyz), _ptr(offsets), int(nvox), _ptr(centres),
+                                   _ptr(lam), _ptr(sf2), _ptr(sn2), _ptr(axis), _ptr(mean),
+                                   _ptr(var), _ptr(status), _ptr(pos), _ptr(scale), _ptr(quat),
+                                   int(flags), _stream(stream))
+    _check("gp_voxels_solve_csr", rc)
+
+
+def gp_voxels_init_gaussians(h, nvox, axis, centres, sf2, mean, var, status, pos, scale, quat,
+                             stream=None) -> None:
+    rc = lib().gp_voxels_init_gaussians(h, int(nvox), _ptr(axis), _ptr(centres), _ptr(sf2),
+                                        _ptr(mean), _ptr(var), _ptr(status), _ptr(pos),
+                                        _ptr(scale), _ptr(quat), _stream(stream))
+    _check("gp_voxels_init_gaussians", rc)
+
+
+# ---- convenience wrapper ------------------------------------------------------------
+class GpVoxels:
+    """Owns one library handle; allocates output tensors with torch."""
+
+    def __init__(self, cfg: gp_voxels_config | None = None, **overrides):
+        self.cfg = cfg if cfg is not None else gp_voxels_config_default(**overrides)
+        if cfg is not None:
+            for k, v in overrides.items():
+                setattr(self.cfg, k, v)
+        self.h = gp_voxels_create(self.cfg)
+
+    def close(self):
+        if self.h is not None:
+            gp_voxels_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, nvox: int, device="cuda", init: bool = False) -> dict:
+        G = self.cfg.grid_side
+        ng = self.cfg.n_s * self.cfg.n_s
+        out = {
+            "axis": torch.empty(nvox, dtype=torch.uint8, device=device),
+            "mean": torch.empty(nvox, G * G, dtype=torch.float32, device=device),
+            "var": torch.empty(nvox, G * G, dtype=torch.float32, device=device),
+            "status": torch.empty(nvox, dtype=torch.int32, device=device),
+        }
+        if init:
+            out["pos"] = torch.empty(nvox * ng, 3, dtype=torch.float32, device=device)
+            out["scale"] = torch.empty(nvox * ng, 3, dtype=torch.float32, device=device)
+            out["quat"] = torch.empty(nvox * ng, 4, dtype=torch.float32, device=device)
+        return out
+
+    def solve_csr(self, xyz, offsets, centres, lam, sf2, sn2, out=None, init=False,
+                  one_per_launch=False, stream=None) -> dict:
+        nvox = offsets.shape[0] - 1
+        if out is None:
+            out = self.outputs(nvox, xyz.device, init)
+        gp_voxels_solve_csr(self.h, xyz, offsets, nvox, centres, lam, sf2, sn2, out["axis"],
+                            out["mean"], out["var"], out["status"], out.get("pos"),
+                            out.get("scale"), out.get("quat"),
+                            SOLVE_ONE_PER_LAUNCH if one_per_launch else 0, stream)
+        return out
+
+    def init_gaussians(self, axis, centres, sf2, mean, var, status=None, stream=None) -> dict:
+        nvox = axis.shape[0]
+        ng = self.cfg.n_s * self.cfg.n_s
+        dev = mean.device
+        out = {
+            "pos": torch.empty(nvox * ng, 3, dtype=torch.float32, device=dev),
+            "scale": torch.empty(nvox * ng, 3, dtype=torch.float32, device=dev),
+            "quat": torch.empty(nvox * ng, 4, dtype=torch.float32, device=dev),
+        }
+        gp_voxels_init_gaussians(self.h, nvox, axis, centres, sf2, mean, var, status, out["pos"],
+                                 out["scale"], out["quat"], stream)
+        return out
+
+
+def batch_to_device(b, device="cuda") -> dict:
+    """Copy a synthetic CSR batch (numpy arrays) to device tensors."""
+    return {
+        "xyz": torch.from_numpy(b.xyz).to(device),
+        "offsets": torch.from_numpy(b.offsets).to(device),
+        "centres": torch.from_numpy(b.centres).to(device),
+        "lam": torch.from_numpy(b.lam).to(device),
+        "sf2": torch.from_numpy(b.sf2).to(device),
+        "sn2": torch.from_numpy(b.sn2).to(device),
+    }
