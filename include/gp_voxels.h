@@ -89,8 +89,17 @@ typedef struct {
     int init_mode;       /* 0: scale = sqrt(eig Phi), rotation = eigenvectors;
                             1: Eq. 8 as printed, S = diag(Phi), R = identity */
     float esc_cond;      /* escalation threshold on (max L_ii / min L_ii)^2 */
-    uint32_t hash_capacity; /* voxel slots of the device hash (power of two) */
-    size_t mem_budget;   /* bytes the handle may allocate (0 = no limit) */
+    uint32_t hash_capacity; /* voxel slots of the device hash (power of two);
+                            0 = no voxel store (batch solves only) */
+    size_t mem_budget;   /* bytes the handle may allocate at create (0 = no limit) */
+    /* serving (used only when hash_capacity > 0) */
+    int scan_slots;      /* scans that may be in flight at once (1..64) */
+    int max_scan_points; /* points per scan (<= 2^20) */
+    int max_scan_voxels; /* visited voxels per scan = rows of a serving solve */
+    int64_t snap_points; /* points of one scan's solve snapshot
+                            (0 = max_scan_voxels * max_points) */
+    float lambda, sf2, sn2; /* kernel and noise of the serving solve (Sec. 3.1 uses
+                            lambda = 1 and no signal variance, sf2 = 1) */
 } gp_voxels_config;
 
 /* Fill *cfg with the paper's defaults (size 0.2, n_s = n_r = 3, tau = 10, lambda 1
@@ -143,6 +152,59 @@ GPV_API int gp_voxels_init_gaussians(gp_voxels_t* h, int32_t nvox, const uint8_t
                              const float* d_centres, const float* d_sf2, const float* d_mean,
                              const float* d_var, const uint32_t* d_status, float* d_pos,
                              float* d_scale, float* d_quat, gpv_stream_t stream);
+
+/* ---- serving: the voxel store of Alg. 2 and re-solves of visited voxels ---------
+ * A handle created with hash_capacity > 0 keeps, on the device, an open-addressing
+ * hash from voxel key floor(p / s) (FP32, IEEE division) to a bucket of at most
+ * max_points points per voxel.  A full bucket drops its oldest points; the points of a
+ * bucket are kept in (scan, index-in-scan) order, so results do not depend on how
+ * concurrent work interleaves.  scan_slots slots hold the state of the scans in
+ * flight; their memory is reserved at create (and counted against mem_budget), so
+ * admitting a scan is admitting it by memory.  Each slot has its own solve workspace:
+ * solves of different slots may run concurrently on different streams.
+ */
+
+/* ALG.STORE (supplementary Alg. 2) for one LiDAR scan: every point is pushed into the
+ * bucket of its voxel and the visited voxels form S_updated (each listed once, in the
+ * order of their first point in the scan).  The call then copies the buckets of the
+ * visited voxels (points after this scan) into the scan's slot, so a later
+ * gp_voxels_solve of the slot sees exactly this state, whatever later scans insert.
+ * Inserts are ordered by call order across all streams.
+ * d_xyz: device FP32 [npts, 3] world points, caller-owned, read on `stream`.
+ * *slot_out: the slot holding this scan until gp_voxels_release_scan.
+ * Errors: GPV_EINVAL (no store, NULL, npts < 0 or > max_scan_points), GPV_EFULL (every
+ * slot is in use: release one and retry), GPV_ECUDA.  A full hash, a scan visiting
+ * more than max_scan_voxels voxels or a full snapshot are reported by
+ * gp_voxels_scan_info, not as errors. */
+GPV_API int gp_voxels_insert_scan(gp_voxels_t* h, const float* d_xyz, int64_t npts,
+                                  uint64_t scan_id, gpv_stream_t stream, int32_t* slot_out);
+
+/* Voxel-GPR of the visited voxels of a slot (Alg. 1 body over S_updated), rows in
+ * S_updated order: the same outputs as gp_voxels_solve_csr, with buffers of
+ * max_scan_voxels rows (the row count stays on the device; gp_voxels_scan_info returns
+ * it), plus optional d_keys [rows] (packed voxel keys, 21 bits per axis, offset 2^20)
+ * and d_centres [rows, 3].  Kernel and noise are the config's lambda, sf2, sn2.
+ * Voxels whose bucket dropped points carry GPV_VOX_TRUNCATED.  No host sync.
+ * Errors: GPV_EINVAL (bad slot, NULL output), GPV_ECUDA. */
+GPV_API int gp_voxels_solve(gp_voxels_t* h, int32_t slot, uint8_t* d_axis, float* d_mean,
+                            float* d_var, uint32_t* d_status, float* d_pos, float* d_scale,
+                            float* d_quat, int64_t* d_keys, float* d_centres,
+                            gpv_stream_t stream);
+
+/* Counts of a slot's scan: rows (visited voxels, at most max_scan_voxels), snapshot
+ * points, flags (bit 0: hash full, points dropped; bit 1: more than max_scan_voxels
+ * visited; bit 2: snapshot full).  Synchronises `stream`.  Errors: GPV_EINVAL, GPV_ECUDA. */
+GPV_API int gp_voxels_scan_info(gp_voxels_t* h, int32_t slot, gpv_stream_t stream,
+                                int32_t* h_rows, int64_t* h_points, uint32_t* h_flags);
+
+/* Give a slot back.  It is reused only after the work queued on `stream` so far has
+ * completed (no host wait), so pass the stream that read the slot's outputs.
+ * Errors: GPV_EINVAL, GPV_ECUDA. */
+GPV_API int gp_voxels_release_scan(gp_voxels_t* h, int32_t slot, gpv_stream_t stream);
+
+/* Voxels currently held by the store (synchronises the device).  Errors: GPV_EINVAL,
+ * GPV_ECUDA. */
+GPV_API int gp_voxels_store_voxels(gp_voxels_t* h, int64_t* h_voxels);
 
 /* Device bytes a handle with this config allocates at create (solve workspaces and
  * the voxel store).  Errors: GPV_EINVAL. */

@@ -45,29 +45,37 @@ struct PrecPlan {
     int nmax_smem = 0;
 };
 
+// Work queues, workspace and streams of one solve in flight.  The CSR entry owns one;
+// every serving scan slot owns another, so solves of different scans overlap safely.
+struct SolveCtx {
+    int cap = 0;                    // rows
+    int32_t* d_bcount = nullptr;
+    int32_t* d_bbase = nullptr;
+    int32_t* d_bcursor = nullptr;
+    int32_t* d_next = nullptr;      // kNumBuckets + 2 dequeue counters
+    int32_t* d_work = nullptr;      // cap
+    int32_t* d_esc_list = nullptr;  // 2 * cap
+    int32_t* d_esc_count = nullptr; // 2
+    void* d_gws = nullptr;
+    cudaStream_t side[kNumBuckets] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kNumBuckets] = {};
+};
+
 }  // namespace
 
 struct gp_voxels {
     gp_voxels_config cfg;
     int dev = 0, sms = 0, Gp = 0;
     PrecPlan plan[3];
-    int32_t* d_bcount = nullptr;
-    int32_t* d_bbase = nullptr;
-    int32_t* d_bcursor = nullptr;
-    int32_t* d_next = nullptr;      // kNumBuckets + 2 dequeue counters
-    int32_t* d_work = nullptr;      // max_voxels
-    int32_t* d_esc_list = nullptr;  // 2 * max_voxels
-    int32_t* d_esc_count = nullptr; // 2
+    SolveCtx main;
+    SolveCtx* sctx = nullptr;       // one per scan slot
     int32_t* d_one = nullptr;       // constant 1 (one-per-launch baseline)
     int32_t* d_ident = nullptr;     // 0..max_voxels-1
     int32_t* d_pl_next = nullptr;   // max_voxels counters (one-per-launch baseline)
-    void* d_gws = nullptr;
     int64_t gws_stride = 0;         // elements (8-byte) per slice
     int gws_grid = 0;
     int esc_grid_small = 0, esc_smem_small = 0, esc_grid_big = 0, esc_smem_big = 0;
-    cudaStream_t side[kNumBuckets] = {};
-    cudaEvent_t ev_fork = nullptr;
-    cudaEvent_t ev_join[kNumBuckets] = {};
     size_t bytes = 0;
     gpv_store* store = nullptr;
 };
@@ -92,6 +100,15 @@ static int validate(const gp_voxels_config* c)
     if (c->init_mode < 0 || c->init_mode > 1) return GPV_EINVAL;
     if (!(c->esc_cond > 1.f)) return GPV_EINVAL;
     if (c->hash_capacity & (c->hash_capacity - 1)) return GPV_EINVAL;
+    if (c->hash_capacity > 0) {
+        if (c->scan_slots < 1 || c->scan_slots > 64) return GPV_EINVAL;
+        if (c->max_scan_points < 1 || c->max_scan_points > (1 << 20)) return GPV_EINVAL;
+        if (c->max_scan_voxels < 1 || c->max_scan_voxels > c->max_voxels ||
+            c->max_scan_voxels >= (1 << 20) - 1)
+            return GPV_EINVAL;
+        if (c->snap_points < 0) return GPV_EINVAL;
+        if (!(c->lambda > 0.f) || !(c->sf2 > 0.f) || !(c->sn2 >= 0.f)) return GPV_EINVAL;
+    }
     return GPV_OK;
 }
 
@@ -154,16 +171,30 @@ extern "C" int gp_voxels_config_default(gp_voxels_config* c)
     c->esc_cond = 1e7f;
     c->hash_capacity = 0;
     c->mem_budget = 0;
+    c->scan_slots = 4;
+    c->max_scan_points = 1 << 17;
+    c->max_scan_voxels = 1 << 16;
+    c->snap_points = 0;
+    c->lambda = 1.f;
+    c->sf2 = 1.f;
+    c->sn2 = 4e-4f;
     return GPV_OK;
+}
+
+static size_t ctx_bytes(const gp_voxels_config* c, int cap, int sms, int Gp)
+{
+    size_t b = 4 * sizeof(int32_t) * (kNumBuckets + 2) + 2 * sizeof(int32_t);
+    b += sizeof(int32_t) * (size_t)cap * 3;  // work, escalation lists
+    b += 8 * (size_t)gws_slice_elems(c->max_points, c->grid_side, Gp) * (size_t)(2 * sms);
+    return b;
 }
 
 static size_t solve_bytes(const gp_voxels_config* c, int sms, int Gp)
 {
-    const size_t mv = (size_t)c->max_voxels;
-    size_t b = 0;
-    b += 4 * sizeof(int32_t) * (kNumBuckets + 2);
-    b += sizeof(int32_t) * mv * 5;  // work, esc (2x), ident, per-launch counters
-    b += 8 * (size_t)gws_slice_elems(c->max_points, c->grid_side, Gp) * (size_t)(2 * sms);
+    size_t b = ctx_bytes(c, c->max_voxels, sms, Gp);
+    b += sizeof(int32_t) * ((size_t)c->max_voxels * 2 + 1);  // ident, per-launch counters
+    if (c->hash_capacity > 0)
+        b += (size_t)c->scan_slots * ctx_bytes(c, c->max_scan_voxels, sms, Gp);
     return b;
 }
 
@@ -177,20 +208,60 @@ extern "C" int gp_voxels_query_sizes(const gp_voxels_config* c, size_t* bytes_ou
     return GPV_OK;
 }
 
+static void ctx_release(SolveCtx& x)
+{
+    cudaFree(x.d_bcount); cudaFree(x.d_bbase); cudaFree(x.d_bcursor); cudaFree(x.d_next);
+    cudaFree(x.d_work); cudaFree(x.d_esc_list); cudaFree(x.d_esc_count); cudaFree(x.d_gws);
+    for (int i = 0; i < kNumBuckets; ++i) {
+        if (x.side[i]) cudaStreamDestroy(x.side[i]);
+        if (x.ev_join[i]) cudaEventDestroy(x.ev_join[i]);
+    }
+    if (x.ev_fork) cudaEventDestroy(x.ev_fork);
+    x = SolveCtx();
+}
+
 static void release(gp_voxels_t* h)
 {
     if (!h) return;
     for (auto& P : h->plan) cudaFree(P.d_hi);
-    cudaFree(h->d_bcount); cudaFree(h->d_bbase); cudaFree(h->d_bcursor); cudaFree(h->d_next);
-    cudaFree(h->d_work); cudaFree(h->d_esc_list); cudaFree(h->d_esc_count); cudaFree(h->d_one);
-    cudaFree(h->d_ident); cudaFree(h->d_pl_next); cudaFree(h->d_gws);
-    for (int i = 0; i < kNumBuckets; ++i) {
-        if (h->side[i]) cudaStreamDestroy(h->side[i]);
-        if (h->ev_join[i]) cudaEventDestroy(h->ev_join[i]);
+    ctx_release(h->main);
+    if (h->sctx) {
+        for (int i = 0; i < h->cfg.scan_slots; ++i) ctx_release(h->sctx[i]);
+        delete[] h->sctx;
     }
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    cudaFree(h->d_one); cudaFree(h->d_ident); cudaFree(h->d_pl_next);
     store_destroy(h->store);
     delete h;
+}
+
+static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap)
+{
+    auto alloc = [&](void** p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return GPV_ENOMEM; }
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->bytes += bytes;
+        return GPV_OK;
+    };
+    int rc;
+#define AL(p, b) if ((rc = alloc((void**)&(p), (b))) != GPV_OK) return rc
+    x.cap = cap;
+    AL(x.d_bcount, sizeof(int32_t) * (kNumBuckets + 2));
+    AL(x.d_bbase, sizeof(int32_t) * (kNumBuckets + 2));
+    AL(x.d_bcursor, sizeof(int32_t) * (kNumBuckets + 2));
+    AL(x.d_next, sizeof(int32_t) * (kNumBuckets + 2));
+    AL(x.d_work, sizeof(int32_t) * (size_t)cap);
+    AL(x.d_esc_list, sizeof(int32_t) * (size_t)cap * 2);
+    AL(x.d_esc_count, sizeof(int32_t) * 2);
+    AL(x.d_gws, 8 * (size_t)h->gws_stride * (size_t)h->gws_grid);
+#undef AL
+    CK(cudaMemset(x.d_esc_count, 0, sizeof(int32_t) * 2));
+    for (int i = 0; i < kNumBuckets; ++i) {
+        CK(cudaStreamCreateWithFlags(&x.side[i], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&x.ev_join[i], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&x.ev_fork, cudaEventDisableTiming));
+    return GPV_OK;
 }
 
 __global__ void k_iota(int32_t* p, int n)
@@ -218,22 +289,20 @@ static int create_impl(gp_voxels_t* h)
     };
     int rc;
 #define AL(p, b) if ((rc = alloc((void**)&(p), (b))) != GPV_OK) return rc
-    AL(h->d_bcount, sizeof(int32_t) * (kNumBuckets + 2));
-    AL(h->d_bbase, sizeof(int32_t) * (kNumBuckets + 2));
-    AL(h->d_bcursor, sizeof(int32_t) * (kNumBuckets + 2));
-    AL(h->d_next, sizeof(int32_t) * (kNumBuckets + 2));
-    AL(h->d_work, sizeof(int32_t) * mv);
-    AL(h->d_esc_list, sizeof(int32_t) * mv * 2);
-    AL(h->d_esc_count, sizeof(int32_t) * 2);
     AL(h->d_one, sizeof(int32_t));
     AL(h->d_ident, sizeof(int32_t) * mv);
     AL(h->d_pl_next, sizeof(int32_t) * mv);
-    h->gws_stride = gws_slice_elems(c.max_points, c.grid_side, h->Gp);
-    AL(h->d_gws, 8 * (size_t)h->gws_stride * (size_t)h->gws_grid);
 #undef AL
+    h->gws_stride = gws_slice_elems(c.max_points, c.grid_side, h->Gp);
+    if ((rc = ctx_create(h, h->main, c.max_voxels)) != GPV_OK) return rc;
+    if (c.hash_capacity > 0) {
+        h->sctx = new (std::nothrow) SolveCtx[c.scan_slots];
+        if (!h->sctx) return GPV_ENOMEM;
+        for (int i = 0; i < c.scan_slots; ++i)
+            if ((rc = ctx_create(h, h->sctx[i], c.max_scan_voxels)) != GPV_OK) return rc;
+    }
     const int one = 1;
     CK(cudaMemcpy(h->d_one, &one, sizeof(int), cudaMemcpyHostToDevice));
-    CK(cudaMemset(h->d_esc_count, 0, sizeof(int32_t) * 2));
     k_iota<<<(c.max_voxels + 255) / 256, 256>>>(h->d_ident, c.max_voxels);
     CK(cudaGetLastError());
     for (int k = 0; k < 3; ++k)
@@ -250,11 +319,6 @@ static int create_impl(gp_voxels_t* h)
         CK(solve_occupancy(PREC_F64, false, h->esc_smem_big, &occ));
         h->esc_grid_big = h->gws_grid;
     }
-    for (int i = 0; i < kNumBuckets; ++i) {
-        CK(cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming));
-    }
-    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     if (c.hash_capacity > 0) {
         rc = store_create(&c, &h->store, &h->bytes);
         if (rc != GPV_OK) return rc;
@@ -290,11 +354,12 @@ extern "C" int gp_voxels_destroy(gp_voxels_t* h)
 }
 
 // Shared by the CSR entry and the serving solve: queue one batched solve.
-int gpv_solve_queue(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets, int32_t nvox,
-                    const float* d_centres, const float* d_lambda, const float* d_sf2,
-                    const float* d_sn2, uint8_t* d_axis, float* d_mean, float* d_var,
-                    uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat,
-                    uint32_t flags, cudaStream_t s)
+static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
+                           const int64_t* d_offsets, int32_t nvox, const int32_t* d_nvox,
+                           const float* d_centres, const float* d_lambda, const float* d_sf2,
+                           const float* d_sn2, uint8_t* d_axis, float* d_mean, float* d_var,
+                           uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat,
+                           uint32_t flags, cudaStream_t s)
 {
     const gp_voxels_config& c = h->cfg;
     const int kind = prec_kind(c.precision);
@@ -302,19 +367,19 @@ int gpv_solve_queue(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets
     SolveArgs a;
     memset(&a, 0, sizeof(a));
     a.xyz = d_xyz; a.offsets = d_offsets; a.centres = d_centres;
-    a.lam = d_lambda; a.sf2 = d_sf2; a.sn2 = d_sn2; a.nvox = nvox;
+    a.lam = d_lambda; a.sf2 = d_sf2; a.sn2 = d_sn2; a.nvox = nvox; a.nvox_dev = d_nvox;
     a.size = c.voxel_size; a.G = c.grid_side; a.Gp = h->Gp; a.n_s = c.n_s; a.n_r = c.n_r;
     a.tau = c.tau; a.mean_mode = c.mean_mode; a.init_mode = c.init_mode;
     a.esc_cond = c.esc_cond;
     a.escalate = kind == PREC_FF ? 1 : 0;
     a.axis = d_axis; a.mean = d_mean; a.var = d_var; a.status = d_status;
     a.pos = d_pos; a.scale = d_scale; a.quat = d_quat;
-    a.esc_list = h->d_esc_list; a.esc_count = h->d_esc_count;
-    a.gws = h->d_gws; a.gws_stride = h->gws_stride;
+    a.esc_list = x.d_esc_list; a.esc_count = x.d_esc_count;
+    a.gws = x.d_gws; a.gws_stride = h->gws_stride;
     a.max_points = c.max_points;
     a.nmax_small_f64 = std::min(h->plan[PREC_F64].nmax_smem, c.max_points);
-    CK(launch_classify(a, P.d_hi, P.nb, h->d_bcount, h->d_bbase, h->d_bcursor, h->d_work,
-                       h->d_next, h->d_esc_count, s));
+    CK(launch_classify(a, P.d_hi, P.nb, x.d_bcount, x.d_bbase, x.d_bcursor, x.d_work,
+                       x.d_next, x.d_esc_count, s));
     if (nvox == 0) return GPV_OK;
 
     if (flags & GPV_SOLVE_ONE_PER_LAUNCH) {
@@ -343,40 +408,40 @@ int gpv_solve_queue(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets
     // Batched: one persistent launch per size bucket, buckets on forked streams.
     // Buckets whose factor lives in the global workspace share it, so they run
     // one after another on the first side stream.
-    CK(cudaEventRecord(h->ev_fork, s));
+    CK(cudaEventRecord(x.ev_fork, s));
     int used = 0;
     for (int b = P.nb - 1; b >= 0; --b) {
         const Bucket& B = P.b[b];
         const int si = B.tri_smem ? 1 + b : 0;
-        cudaStream_t ss = h->side[si % kNumBuckets];
-        CK(cudaStreamWaitEvent(ss, h->ev_fork, 0));
-        a.work = h->d_work;
-        a.work_base = h->d_bbase + b;
-        a.work_count = h->d_bcount + b;
-        a.work_next = h->d_next + b;
+        cudaStream_t ss = x.side[si % kNumBuckets];
+        CK(cudaStreamWaitEvent(ss, x.ev_fork, 0));
+        a.work = x.d_work;
+        a.work_base = x.d_bbase + b;
+        a.work_count = x.d_bcount + b;
+        a.work_next = x.d_next + b;
         a.nmax = B.tri_smem ? B.hi : c.max_points;
         CK(launch_solve(kind, B.tri_smem, a, B.grid, B.smem, ss));
         used |= 1 << (si % kNumBuckets);
     }
     for (int i = 0; i < kNumBuckets; ++i)
         if (used & (1 << i)) {
-            CK(cudaEventRecord(h->ev_join[i], h->side[i]));
-            CK(cudaStreamWaitEvent(s, h->ev_join[i], 0));
+            CK(cudaEventRecord(x.ev_join[i], x.side[i]));
+            CK(cudaStreamWaitEvent(s, x.ev_join[i], 0));
         }
     if (kind == PREC_FF) {
         // FP64 re-solve of the voxels that failed the conditioning check
         a.escalate = 0;
         a.escalation_pass = 1;
-        a.work = h->d_esc_list;
+        a.work = x.d_esc_list;
         a.work_base = nullptr;
-        a.work_count = h->d_esc_count;
-        a.work_next = h->d_next + P.nb;
+        a.work_count = x.d_esc_count;
+        a.work_next = x.d_next + P.nb;
         a.nmax = a.nmax_small_f64;
         CK(launch_solve(PREC_F64, true, a, h->esc_grid_small, h->esc_smem_small, s));
         if (c.max_points > a.nmax_small_f64) {
-            a.work = h->d_esc_list + nvox;
-            a.work_count = h->d_esc_count + 1;
-            a.work_next = h->d_next + P.nb + 1;
+            a.work = x.d_esc_list + nvox;
+            a.work_count = x.d_esc_count + 1;
+            a.work_next = x.d_next + P.nb + 1;
             a.nmax = c.max_points;
             CK(launch_solve(PREC_F64, false, a, h->esc_grid_big, h->esc_smem_big, s));
         }
@@ -398,9 +463,9 @@ extern "C" int gp_voxels_solve_csr(gp_voxels_t* h, const float* d_xyz, const int
     const bool any_init = d_pos || d_scale || d_quat;
     if (any_init && !(d_pos && d_scale && d_quat)) return GPV_EINVAL;
     if (flags & ~(uint32_t)GPV_SOLVE_ONE_PER_LAUNCH) return GPV_EINVAL;
-    return gpv_solve_queue(h, d_xyz, d_offsets, nvox, d_centres, d_lambda, d_sf2, d_sn2, d_axis,
-                           d_mean, d_var, d_status, d_pos, d_scale, d_quat, flags,
-                           (cudaStream_t)stream);
+    return gpv_solve_queue(h, h->main, d_xyz, d_offsets, nvox, nullptr, d_centres, d_lambda,
+                           d_sf2, d_sn2, d_axis, d_mean, d_var, d_status, d_pos, d_scale, d_quat,
+                           flags, (cudaStream_t)stream);
 }
 
 extern "C" int gp_voxels_init_gaussians(gp_voxels_t* h, int32_t nvox, const uint8_t* d_axis,
@@ -417,6 +482,93 @@ extern "C" int gp_voxels_init_gaussians(gp_voxels_t* h, int32_t nvox, const uint
     CK(launch_init(d_mean, d_var, d_axis, d_centres, d_sf2, d_status, nvox, c.voxel_size,
                    c.grid_side, c.n_s, c.n_r, c.init_mode, d_pos, d_scale, d_quat,
                    (cudaStream_t)stream));
+    return GPV_OK;
+}
+
+// ---- serving ----------------------------------------------------------------------
+extern "C" int gp_voxels_insert_scan(gp_voxels_t* h, const float* d_xyz, int64_t npts,
+                                     uint64_t scan_id, gpv_stream_t stream, int32_t* slot_out)
+{
+    (void)scan_id;  // inserts are ordered by call order; the id is the caller's label
+    if (!h || !h->store || !slot_out) return GPV_EINVAL;
+    if (npts < 0 || npts > h->cfg.max_scan_points || (npts > 0 && !d_xyz)) return GPV_EINVAL;
+    gpv_store* st = h->store;
+    int si = -1;
+    for (int i = 0; i < st->nslots; ++i)
+        if (!st->slots[i].busy) { si = i; break; }
+    if (si < 0) return GPV_EFULL;
+    cudaStream_t s = (cudaStream_t)stream;
+    gpv_scan_slot& S = st->slots[si];
+    CK(cudaStreamWaitEvent(s, S.free_ev, 0));      // the slot's previous scan is done
+    CK(cudaStreamWaitEvent(s, st->ev_insert, 0));  // inserts follow call order
+    CK(store_insert(st, si, d_xyz, (int)npts, s, &h->cfg));
+    CK(cudaEventRecord(st->ev_insert, s));
+    CK(cudaEventRecord(S.ins_ev, s));
+    S.busy = true;
+    *slot_out = si;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_solve(gp_voxels_t* h, int32_t slot, uint8_t* d_axis, float* d_mean,
+                               float* d_var, uint32_t* d_status, float* d_pos, float* d_scale,
+                               float* d_quat, int64_t* d_keys, float* d_centres,
+                               gpv_stream_t stream)
+{
+    if (!h || !h->store || slot < 0 || slot >= h->store->nslots || !h->store->slots[slot].busy)
+        return GPV_EINVAL;
+    if (!d_axis || !d_mean || !d_var || !d_status) return GPV_EINVAL;
+    const bool any_init = d_pos || d_scale || d_quat;
+    if (any_init && !(d_pos && d_scale && d_quat)) return GPV_EINVAL;
+    gpv_store* st = h->store;
+    gpv_scan_slot& S = st->slots[slot];
+    cudaStream_t s = (cudaStream_t)stream;
+    // the slot's insert may have been queued on another stream
+    CK(cudaStreamWaitEvent(s, S.ins_ev, 0));
+    int rc = gpv_solve_queue(h, h->sctx[slot], S.snap, S.snapoff, st->max_vox, S.counters,
+                             S.centres, S.lam, S.sf2, S.sn2, d_axis, d_mean, d_var, d_status,
+                             d_pos, d_scale, d_quat, 0, s);
+    if (rc != GPV_OK) return rc;
+    CK(store_or_flags(st, slot, d_status, s));
+    CK(store_copy_rows(st, slot, d_keys, d_centres, s));
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_scan_info(gp_voxels_t* h, int32_t slot, gpv_stream_t stream,
+                                   int32_t* h_rows, int64_t* h_points, uint32_t* h_flags)
+{
+    if (!h || !h->store || slot < 0 || slot >= h->store->nslots || !h->store->slots[slot].busy)
+        return GPV_EINVAL;
+    gpv_scan_slot& S = h->store->slots[slot];
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t c[4];
+    int64_t np = 0;
+    CK(cudaStreamWaitEvent(s, S.ins_ev, 0));
+    CK(cudaMemcpyAsync(c, S.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&np, S.npoints, sizeof(np), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h_rows) *h_rows = c[0];
+    if (h_points) *h_points = np < h->store->snap_cap ? np : h->store->snap_cap;
+    if (h_flags) *h_flags = (uint32_t)c[1];
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_release_scan(gp_voxels_t* h, int32_t slot, gpv_stream_t stream)
+{
+    if (!h || !h->store || slot < 0 || slot >= h->store->nslots || !h->store->slots[slot].busy)
+        return GPV_EINVAL;
+    gpv_scan_slot& S = h->store->slots[slot];
+    CK(cudaEventRecord(S.free_ev, (cudaStream_t)stream));
+    S.busy = false;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_store_voxels(gp_voxels_t* h, int64_t* h_voxels)
+{
+    if (!h || !h->store || !h_voxels) return GPV_EINVAL;
+    int32_t n = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&n, h->store->nvox, sizeof(n), cudaMemcpyDeviceToHost));
+    *h_voxels = n;
     return GPV_OK;
 }
 

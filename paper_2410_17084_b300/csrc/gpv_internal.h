@@ -31,7 +31,8 @@ struct SolveArgs {
     const float* lam;
     const float* sf2;
     const float* sn2;
-    int32_t nvox;
+    int32_t nvox;               // rows of the outputs (stride of the escalation lists)
+    const int32_t* nvox_dev;    // device count of rows to solve (serving), or null
     float size;
     int G, Gp, n_s, n_r, tau, mean_mode, init_mode;
     float esc_cond;

@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveArgs A)
 __global__ void k_classify(SolveArgs A, const int* bucket_hi, int nb, int32_t* bcount)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= A.nvox) return;
+    if (v >= (A.nvox_dev ? min(*A.nvox_dev, A.nvox) : A.nvox)) return;
     const int64_t n = A.offsets[v + 1] - A.offsets[v];
     if (n < A.tau || n <= 0 || n > A.max_points) {
         const int GG = A.G * A.G;
@@ -477,7 +477,7 @@ __global__ void k_scatter(SolveArgs A, const int* bucket_hi, int nb, const int32
                           int32_t* bcursor, int32_t* work)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= A.nvox) return;
+    if (v >= (A.nvox_dev ? min(*A.nvox_dev, A.nvox) : A.nvox)) return;
     const int64_t n = A.offsets[v + 1] - A.offsets[v];
     if (n < A.tau || n <= 0 || n > A.max_points) return;
     int b = nb - 1;

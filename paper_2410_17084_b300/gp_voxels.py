@@ -23,7 +23,8 @@ SOLVE_ONE_PER_LAUNCH = 1
 EXPORTED = [
     "gp_voxels_config_default", "gp_voxels_create", "gp_voxels_destroy", "gp_voxels_solve_csr",
     "gp_voxels_init_gaussians", "gp_voxels_query_sizes", "gp_voxels_strerror",
-    "gp_voxels_last_error",
+    "gp_voxels_last_error", "gp_voxels_insert_scan", "gp_voxels_solve", "gp_voxels_scan_info",
+    "gp_voxels_release_scan", "gp_voxels_store_voxels",
 ]
 
 
@@ -42,6 +43,13 @@ class gp_voxels_config(ctypes.Structure):
         ("esc_cond", ctypes.c_float),
         ("hash_capacity", ctypes.c_uint32),
         ("mem_budget", ctypes.c_size_t),
+        ("scan_slots", ctypes.c_int),
+        ("max_scan_points", ctypes.c_int),
+        ("max_scan_voxels", ctypes.c_int),
+        ("snap_points", ctypes.c_int64),
+        ("lambda_", ctypes.c_float),
+        ("sf2", ctypes.c_float),
+        ("sn2", ctypes.c_float),
     ]
 
 
@@ -73,6 +81,14 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_size_t)]
         L.gp_voxels_strerror.argtypes = [I]
         L.gp_voxels_strerror.restype = ctypes.c_char_p
+        L.gp_voxels_insert_scan.argtypes = [P, P, ctypes.c_int64, ctypes.c_uint64, P,
+                                             ctypes.POINTER(ctypes.c_int32)]
+        L.gp_voxels_solve.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P, P, P, P]
+        L.gp_voxels_scan_info.argtypes = [P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_uint32)]
+        L.gp_voxels_release_scan.argtypes = [P, ctypes.c_int32, P]
+        L.gp_voxels_store_voxels.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -148,6 +164,51 @@ def gp_voxels_init_gaussians(h, nvox, axis, centres, sf2, mean, var, status, pos
                                         _ptr(mean), _ptr(var), _ptr(status), _ptr(pos),
                                         _ptr(scale), _ptr(quat), _stream(stream))
     _check("gp_voxels_init_gaussians", rc)
+
+
+def gp_voxels_insert_scan(h, xyz, npts, scan_id=0, stream=None) -> int:
+    """Queue ALG.STORE of one scan; returns the slot, or raises GpvError (EFULL: no free
+    slot)."""
+    slot = ctypes.c_int32(-1)
+    rc = lib().gp_voxels_insert_scan(h, _ptr(xyz) if npts else None, int(npts), int(scan_id),
+                                     _stream(stream), ctypes.byref(slot))
+    _check("gp_voxels_insert_scan", rc)
+    return slot.value
+
+
+def gp_voxels_solve(h, slot, axis, mean, var, status, pos=None, scale=None, quat=None,
+                    keys=None, centres=None, stream=None) -> None:
+    rc = lib().gp_voxels_solve(h, int(slot), _ptr(axis), _ptr(mean), _ptr(var), _ptr(status),
+                               _ptr(pos), _ptr(scale), _ptr(quat), _ptr(keys), _ptr(centres),
+                               _stream(stream))
+    _check("gp_voxels_solve", rc)
+
+
+def gp_voxels_scan_info(h, slot, stream=None) -> tuple[int, int, int]:
+    r, p, f = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_uint32()
+    rc = lib().gp_voxels_scan_info(h, int(slot), _stream(stream), ctypes.byref(r), ctypes.byref(p),
+                                   ctypes.byref(f))
+    _check("gp_voxels_scan_info", rc)
+    return r.value, p.value, f.value
+
+
+def gp_voxels_release_scan(h, slot, stream=None) -> None:
+    _check("gp_voxels_release_scan", lib().gp_voxels_release_scan(h, int(slot), _stream(stream)))
+
+
+def gp_voxels_store_voxels(h) -> int:
+    n = ctypes.c_int64()
+    _check("gp_voxels_store_voxels", lib().gp_voxels_store_voxels(h, ctypes.byref(n)))
+    return n.value
+
+
+def unpack_keys(keys):
+    """Integer voxel indices (kx, ky, kz) of packed keys (21 bits per axis, offset 2^20)."""
+    import numpy as np
+    k = np.asarray(keys, dtype=np.int64)
+    m = (1 << 21) - 1
+    return np.stack([(k & m) - (1 << 20), ((k >> 21) & m) - (1 << 20),
+                     ((k >> 42) & m) - (1 << 20)], axis=-1).astype(np.int32)
 
 
 # ---- convenience wrapper ------------------------------------------------------------

@@ -215,28 +215,50 @@ def lidar_scene(nscans: int = 2000, nboxes: int = 200, seed: int = 3) -> LidarSc
 def lidar_scan(scene: LidarScene, k: int, beams: int = 64, azimuths: int = 1024,
                range_sd: float = 0.02) -> np.ndarray:
     """World-frame points of scan ``k``: 64 beams evenly over [-25, +15] degrees of
-    elevation x 1024 azimuths, ranges clipped to [1, 80] m, Gaussian range noise."""
+    elevation x 1024 azimuths, ranges clipped to [1, 80] m, Gaussian range noise.
+    Rays hit the ground plane z = 0 or the nearest box (slab test); each box is tested
+    only against the azimuth columns its footprint covers as seen from the sensor."""
     rng = np.random.default_rng((scene.seed, k))
     o = scene.path[k]
     el = np.deg2rad(np.linspace(-25.0, 15.0, beams))
-    az = np.linspace(0.0, 2 * np.pi, azimuths, endpoint=False) + rng.uniform(0, 2 * np.pi / azimuths)
+    step = 2 * np.pi / azimuths
+    az0 = rng.uniform(0, step)
+    az = np.arange(azimuths) * step + az0
     ce, se = np.cos(el)[:, None], np.sin(el)[:, None]
     d = np.stack([np.broadcast_to(ce * np.cos(az), (beams, azimuths)),
                   np.broadcast_to(ce * np.sin(az), (beams, azimuths)),
-                  np.broadcast_to(se, (beams, azimuths))], -1).reshape(-1, 3)
-    t = np.full(d.shape[0], np.inf)
-    down = d[:, 2] < 0
-    t[down] = -o[2] / d[down, 2]
-    near = np.linalg.norm((scene.box_lo[:, :2] + scene.box_hi[:, :2]) / 2 - o[:2], axis=1) < 85
+                  np.broadcast_to(se, (beams, azimuths))], -1)  # [beams, az, 3]
+    t = np.full((beams, azimuths), np.inf)
+    down = d[..., 2] < 0
+    t[down] = -o[2] / d[..., 2][down]
+    ctr = (scene.box_lo[:, :2] + scene.box_hi[:, :2]) / 2
+    near = np.nonzero(np.linalg.norm(ctr - o[:2], axis=1) < 90.0)[0]
     with np.errstate(divide="ignore", invalid="ignore"):
-        inv = 1.0 / d
-        for lo, hi in zip(scene.box_lo[near], scene.box_hi[near]):
+        for b in near:
+            lo, hi = scene.box_lo[b], scene.box_hi[b]
+            cx = np.array([lo[0], hi[0], hi[0], lo[0]]) - o[0]
+            cy = np.array([lo[1], lo[1], hi[1], hi[1]]) - o[1]
+            if lo[0] <= o[0] <= hi[0] and lo[1] <= o[1] <= hi[1]:
+                cols = np.arange(azimuths)
+            else:
+                ang = np.arctan2(cy, cx)
+                mid = np.arctan2(ctr[b, 1] - o[1], ctr[b, 0] - o[0])
+                rel = np.angle(np.exp(1j * (ang - mid)))  # corner angles around the centre
+                a_lo, a_hi = mid + rel.min() - step, mid + rel.max() + step
+                i0 = int(np.floor((a_lo - az0) / step))
+                i1 = int(np.ceil((a_hi - az0) / step))
+                cols = np.arange(i0, i1 + 1) % azimuths
+            dd = d[:, cols, :]
+            inv = 1.0 / dd
             t1 = (lo - o) * inv
             t2 = (hi - o) * inv
-            tmin = np.nanmax(np.minimum(t1, t2), axis=1)
-            tmax = np.nanmin(np.maximum(t1, t2), axis=1)
+            tmin = np.nanmax(np.minimum(t1, t2), axis=-1)
+            tmax = np.nanmin(np.maximum(t1, t2), axis=-1)
             hit = (tmax >= np.maximum(tmin, 0.0)) & (tmin > 0)
-            t = np.where(hit & (tmin < t), tmin, t)
+            tc = t[:, cols]
+            t[:, cols] = np.where(hit & (tmin < tc), tmin, tc)
+    t = t.reshape(-1)
+    d = d.reshape(-1, 3)
     ok = (t >= 1.0) & (t <= 80.0)
     r = t[ok] + range_sd * rng.standard_normal(int(ok.sum()))
     pts = o + d[ok] * r[:, None]

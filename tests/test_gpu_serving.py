@@ -1,0 +1,121 @@
+"""Serving path on the GPU: the device voxel store (ALG.STORE / ALG.HASH of the
+supplementary Alg. 2) and the re-solve of visited voxels, against the oracle's store and
+FP64 Voxel-GPR; identical results alone and in the mix of concurrent scans; admission
+by free scan slots; per-scan latency at 10 Hz arrivals."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+MEAN_TOL = 1e-4
+VAR_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_17084_b300 import build, gp_voxels as gv, serve, synth
+    build.build()
+    scene = synth.lidar_scene(nscans=2000, seed=3)
+    scans = [synth.lidar_scan(scene, k) for k in range(6)]
+    return gv, serve, synth, scene, scans
+
+
+def _cfg(serve, **kw):
+    d = dict(hash_capacity=1 << 18, max_points=64, scan_slots=4, max_scan_points=1 << 16,
+             max_scan_voxels=1 << 14, snap_points=1 << 20, mem_budget=0)
+    d.update(kw)
+    return serve.serving_config(**d)
+
+
+def test_store_and_solve_match_oracle(env, oracle):
+    from oracle import compare
+    gv, serve, synth, scene, scans = env
+    cfg = _cfg(serve)
+    srv = serve.Server(cfg)
+    lat, wall, res = srv.run(scans[:3], collect=True, realtime=False, max_inflight=1)
+    srv.close()
+    store = oracle.VoxelStore(cfg.voxel_size, cfg.max_points)
+    for k in range(3):
+        touched = store.insert_scan(scans[k])
+        r = res[k]
+        assert r["flags"] == 0
+        keys = gv.unpack_keys(r["keys"])
+        assert r["rows"] == len(touched)
+        assert np.array_equal(keys, np.array(touched, dtype=np.int32)), "S_updated order"
+        pts = [store.points(t) for t in touched]
+        counts = np.array([p.shape[0] for p in pts], dtype=np.int64)
+        off = np.zeros(len(pts) + 1, np.int64)
+        off[1:] = np.cumsum(counts)
+        cen = oracle.voxel_centres(np.array(touched, np.int32), cfg.voxel_size)
+        assert np.array_equal(cen, r["centres"])
+        nv = len(pts)
+        b = synth.VoxelBatch("scan", np.concatenate(pts).astype(np.float32), off, cen,
+                             np.full(nv, cfg.lambda_, np.float32), np.full(nv, cfg.sf2, np.float32),
+                             np.full(nv, cfg.sn2, np.float32), cfg.voxel_size, cfg.grid_side,
+                             cfg.n_s, cfg.n_r, cfg.tau, counts, np.zeros(nv, bool))
+        st = r["status"].astype(np.uint32)
+        trunc = np.array([store.total[t] > cfg.max_points for t in touched])
+        assert np.array_equal((st & gv.VOX_TRUNCATED) != 0, trunc)
+        ax = r["axis"].astype(np.int32)
+        ref = compare.oracle_for_batch(b, gpu_axis=np.where(ax <= 2, ax, -1))
+        solved = ref["status"] == 0
+        assert np.array_equal(solved, (st & (gv.VOX_BELOW_TAU | gv.VOX_NOT_SPD)) == 0)
+        err = compare.gpr_errors(r["mean"], r["var"], ref, b.sn2, solved)
+        print(f"\nscan {k}: rows {nv} solved {int(solved.sum())} truncated {int(trunc.sum())} {err}")
+        assert err["mean_max"] <= MEAN_TOL and err["var_max"] <= VAR_TOL
+
+
+def test_same_result_alone_and_in_the_mix(env):
+    """Every scan gives bit-identical outputs whether it runs alone or while other scans'
+    inserts and solves are in flight on other streams."""
+    gv, serve, synth, scene, scans = env
+    outs = []
+    for inflight in (1, 4):
+        srv = serve.Server(_cfg(serve))
+        lat, wall, res = srv.run(scans, collect=True, realtime=False, max_inflight=inflight)
+        srv.close()
+        outs.append(res)
+    for k in range(len(scans)):
+        for key in ("axis", "mean", "var", "status", "keys", "pos", "scale", "quat"):
+            assert np.array_equal(outs[0][k][key], outs[1][k][key]), (k, key)
+
+
+def test_admission_by_free_slots(env):
+    import torch
+    gv, serve, synth, scene, scans = env
+    g = gv.GpVoxels(_cfg(serve, scan_slots=2))
+    x = torch.from_numpy(scans[0]).cuda()
+    s0 = gv.gp_voxels_insert_scan(g.h, x, x.shape[0], 0)
+    s1 = gv.gp_voxels_insert_scan(g.h, x, x.shape[0], 1)
+    with pytest.raises(gv.GpvError) as ei:
+        gv.gp_voxels_insert_scan(g.h, x, x.shape[0], 2)
+    assert ei.value.code == gv.GPV_EFULL
+    gv.gp_voxels_release_scan(g.h, s0)
+    s2 = gv.gp_voxels_insert_scan(g.h, x, x.shape[0], 2)
+    assert s2 == s0 and s1 != s0
+    rows, npts, flags = gv.gp_voxels_scan_info(g.h, s2)
+    assert rows > 0 and flags == 0
+    assert gv.gp_voxels_store_voxels(g.h) >= rows
+    g.close()
+
+
+def test_budget_rejects_oversized_store(env):
+    gv, serve, synth, scene, scans = env
+    with pytest.raises(gv.GpvError) as ei:
+        gv.GpVoxels(_cfg(serve, mem_budget=64 << 20))
+    assert ei.value.code == gv.GPV_EBUDGET
+
+
+def test_realtime_latency_10hz(env):
+    """30 scans arriving at 10 Hz (Poisson): p99 scan latency under 100 ms."""
+    gv, serve, synth, scene, scans = env
+    more = [synth.lidar_scan(scene, k) for k in range(30)]
+    srv = serve.Server(serve.serving_config())
+    lat, wall, _ = srv.run(more, arrivals=scene.arrivals[:30], realtime=True)
+    srv.close()
+    p50, p99 = np.percentile(lat * 1e3, [50, 99])
+    print(f"\nlatency p50 {p50:.2f} ms p99 {p99:.2f} ms over {wall:.1f} s")
+    assert p99 < 100.0
