@@ -206,6 +206,35 @@ GPV_API int gp_voxels_release_scan(gp_voxels_t* h, int32_t slot, gpv_stream_t st
  * GPV_ECUDA. */
 GPV_API int gp_voxels_store_voxels(gp_voxels_t* h, int64_t* h_voxels);
 
+/* ---- allocation-free batched solve -------------------------------------------------
+ * No counterpart in the paper: an entry point for callers that may not allocate device
+ * memory themselves or through this library -- for example code running inside a host
+ * application that owns every device allocation under a fixed memory plan, or an op of
+ * another framework that may only use the tensors it is handed.  It solves a CSR batch
+ * like gp_voxels_solve_csr (same inputs, outputs, layouts and per-voxel status), without
+ * a handle, using a static scratch area that the library holds on every GPU it is loaded
+ * on (about 0.8 MB, kept until the process exits).
+ *  - cfg: the configuration a handle would take (fields of the voxel store and of
+ *    serving are ignored); precision FP32, MIXED or FP64.
+ *  - At most GPV_NOALLOC_MAX_VOXELS voxels per call; larger batches get GPV_EINVAL.
+ *  - Voxels whose factor does not fit shared memory (in FP32 about 256 points at
+ *    G <= 16; in the 8-byte precisions about 176) are not solved and get
+ *    GPV_VOX_TOO_LARGE; gp_voxels_solve_csr handles them.
+ *  - The first call on a device looks up the scratch area's device address; make that
+ *    first call before capturing a stream.
+ *  - All calls share the scratch area: calls whose GPU work overlaps (on different
+ *    streams, or from several threads) race and give wrong results.  Serialise them.
+ *  - No cudaMalloc, cudaFree or other allocating call is made.
+ * Errors: GPV_EINVAL (bad config, NULL, nvox out of range), GPV_ECUDA. */
+#define GPV_NOALLOC_MAX_VOXELS 65536
+GPV_API int gp_voxels_solve_csr_noalloc(const gp_voxels_config* cfg, const float* d_xyz,
+                                        const int64_t* d_offsets, int32_t nvox,
+                                        const float* d_centres, const float* d_lambda,
+                                        const float* d_sf2, const float* d_sn2,
+                                        uint8_t* d_axis, float* d_mean, float* d_var,
+                                        uint32_t* d_status, float* d_pos, float* d_scale,
+                                        float* d_quat, gpv_stream_t stream);
+
 /* Device bytes a handle with this config allocates at create (solve workspaces and
  * the voxel store).  Errors: GPV_EINVAL. */
 GPV_API int gp_voxels_query_sizes(const gp_voxels_config* cfg, size_t* bytes_out);

@@ -587,3 +587,5 @@ extern "C" const char* gp_voxels_strerror(int s)
 }
 
 extern "C" const char* gp_voxels_last_error(void) { return g_last_err; }
+
+void gpv::gpv_record_cuda_error(cudaError_t e) { cuda_fail(e); }

@@ -100,6 +100,9 @@ __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize
     return p;
 }
 
+// Text of a CUDA error for gp_voxels_last_error() (gpv_api.cu)
+void gpv_record_cuda_error(cudaError_t e);
+
 // Launchers (gpv_solve.cu)
 cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, int32_t* bcount,
                             int32_t* bbase, int32_t* bcursor, int32_t* work, int32_t* next,

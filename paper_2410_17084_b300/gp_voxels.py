@@ -24,8 +24,9 @@ EXPORTED = [
     "gp_voxels_config_default", "gp_voxels_create", "gp_voxels_destroy", "gp_voxels_solve_csr",
     "gp_voxels_init_gaussians", "gp_voxels_query_sizes", "gp_voxels_strerror",
     "gp_voxels_last_error", "gp_voxels_insert_scan", "gp_voxels_solve", "gp_voxels_scan_info",
-    "gp_voxels_release_scan", "gp_voxels_store_voxels",
+    "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
 ]
+NOALLOC_MAX_VOXELS = 65536
 
 
 class gp_voxels_config(ctypes.Structure):
@@ -89,6 +90,9 @@ def lib() -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_uint32)]
         L.gp_voxels_release_scan.argtypes = [P, ctypes.c_int32, P]
         L.gp_voxels_store_voxels.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        L.gp_voxels_solve_csr_noalloc.argtypes = [ctypes.POINTER(gp_voxels_config), P, P,
+                                                  ctypes.c_int32, P, P, P, P, P, P, P, P, P,
+                                                  P, P, P]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -156,6 +160,19 @@ def gp_voxels_solve_csr(h, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, mea
                                    _ptr(var), _ptr(status), _ptr(pos), _ptr(scale), _ptr(quat),
                                    int(flags), _stream(stream))
     _check("gp_voxels_solve_csr", rc)
+
+
+def gp_voxels_solve_csr_noalloc(cfg, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, mean,
+                                var, status, pos=None, scale=None, quat=None,
+                                stream=None) -> None:
+    """The batched solve without a handle and without any device allocation: the
+    library's static scratch area holds its work queues (see include/gp_voxels.h)."""
+    rc = lib().gp_voxels_solve_csr_noalloc(ctypes.byref(cfg), _ptr(xyz), _ptr(offsets),
+                                           int(nvox), _ptr(centres), _ptr(lam), _ptr(sf2),
+                                           _ptr(sn2), _ptr(axis), _ptr(mean), _ptr(var),
+                                           _ptr(status), _ptr(pos), _ptr(scale), _ptr(quat),
+                                           _stream(stream))
+    _check("gp_voxels_solve_csr_noalloc", rc)
 
 
 def gp_voxels_init_gaussians(h, nvox, axis, centres, sf2, mean, var, status, pos, scale, quat,
