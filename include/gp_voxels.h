@@ -81,7 +81,7 @@ typedef struct {
     int grid_side;       /* G = n_s * n_r query nodes per side (Sec. 3.2); 1..32 */
     int n_s, n_r;        /* Gaussians per voxel side, nodes per Gaussian side */
     int tau;             /* minimum points per voxel (Sec. 3.1, tau = 10) */
-    int max_points;      /* largest n per voxel accepted by the solve; also the
+    int max_points;      /* largest n per voxel accepted by the solve (<= 1024); also the
                             bucket capacity of the voxel store */
     int max_voxels;      /* largest batch (voxels) per solve call */
     int mean_mode;       /* 0: zero prior mean (Eq. 2); 1: data mean of f */

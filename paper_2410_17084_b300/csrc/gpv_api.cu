@@ -93,7 +93,7 @@ static int validate(const gp_voxels_config* c)
     if (!(c->voxel_size > 0.f)) return GPV_EINVAL;
     if (c->grid_side < 1 || c->grid_side > kMaxG) return GPV_EINVAL;
     if (c->n_s < 1 || c->n_r < 1 || c->n_s * c->n_r != c->grid_side) return GPV_EINVAL;
-    if (c->tau < 1 || c->max_points < c->tau || c->max_points > 2048) return GPV_EINVAL;
+    if (c->tau < 1 || c->max_points < c->tau || c->max_points > 1024) return GPV_EINVAL;
     if (c->max_voxels < 1) return GPV_EINVAL;
     if (c->mean_mode < 0 || c->mean_mode > 1) return GPV_EINVAL;
     if (c->precision < 0 || c->precision > 2) return GPV_EINVAL;
@@ -141,8 +141,10 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         hi_host[i] = B.hi;
         B.tri_smem = B.hi <= P.nmax_smem;
         // the workspace variant lays out its slice for max_points, whatever the bucket
-        B.smem = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp, tsize(kind),
-                           B.tri_smem).total;
+        const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
+                                      tsize(kind), B.tri_smem);
+        if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) return GPV_EINVAL;  // panels too thin
+        B.smem = sp.total;
         int occ = 0;
         CK(solve_occupancy(kind, B.tri_smem, B.smem, &occ));
         if (occ < 1) return GPV_EINVAL;

@@ -69,9 +69,14 @@ __host__ __device__ inline int64_t gws_slice_elems(int nmax, int G, int Gp)
 }
 
 struct SmemPlan {
-    int off_pts, off_vec, off_tri, off_a, off_b, off_part, off_mv, total;
+    int off_pts, off_vec, off_tri, off_a, off_b, off_part, off_mv, off_work, total;
     int nrg, nqg;
+    int pb, rb;  // panel width of the blocked factor, row block of the blocked inverse
 };
+
+// Shared memory of the workspace variant (factor in global memory): its panel buffers
+// take what the other regions leave of this budget.
+constexpr int kBigSmem = 216 * 1024;
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
@@ -96,6 +101,20 @@ __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize
     if (tri_in_smem) o = align16(o + nmax * Gp * tsize);
     p.off_part = o; o = align16(o + nrg * G * Gp * tsize);
     p.off_mv = o; o = align16(o + 2 * G * G * 8);
+    p.off_work = o;
+    p.pb = 0;
+    p.rb = 0;
+    if (!tri_in_smem) {
+        const int work = kBigSmem - o;
+        int pb = work > 0 ? work / (2 * nmax * tsize) : 0;
+        int rb = work > 0 ? work / (nmax * tsize) : 0;
+        pb = (pb > 32 ? 32 : pb) & ~3;
+        rb = (rb > 16 ? 16 : rb) & ~3;
+        p.pb = pb;
+        p.rb = rb;
+        const int need = (2 * pb > rb ? 2 * pb : rb) * nmax * tsize;
+        o = align16(o + need);
+    }
     p.total = o;
     return p;
 }

@@ -79,6 +79,134 @@ __device__ inline int value_axis_from_cov(const float c6[6])
     return ax;
 }
 
+// ---- blocked factor and inverse for voxels whose triangle lives in global memory ----
+// The triangle (column-major packed, element (r, c) at tri_off(c, n) + r - c) stays in
+// the CTA's workspace slice; panels of it are staged in shared memory so that every
+// inner loop runs on shared memory and the global traffic is streamed, not latency-bound.
+
+// Left-looking Cholesky by panels of pb columns: for each panel, stage the Gram columns,
+// subtract the products of all finished columns (streamed through a tile of pb columns),
+// factor the panel in shared memory, write it back.  Returns false at a non-positive
+// pivot.  P and Tt hold pb x (n - p0) values each.
+template <class T>
+__device__ bool big_cholesky(T* L, int n, T* P, T* Tt, int pb, float& dmin, float& dmax)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int p0 = 0; p0 < n; p0 += pb) {
+        const int pw = min(pb, n - p0), R = n - p0;
+        __syncthreads();
+        for (int idx = tid; idx < pw * R; idx += nthr) {
+            const int c = idx / R, r = idx - c * R;
+            if (r >= c) P[idx] = L[tri_off(p0 + c, n) + (r - c)];
+        }
+        for (int k0 = 0; k0 < p0; k0 += pb) {
+            const int kw = min(pb, p0 - k0);
+            __syncthreads();
+            for (int idx = tid; idx < kw * R; idx += nthr) {
+                const int kk = idx / R, r = idx - kk * R;
+                Tt[idx] = L[tri_off(k0 + kk, n) + (p0 - k0 - kk) + r];
+            }
+            __syncthreads();
+            for (int r = tid; r < R; r += nthr) {
+                for (int cg = 0; cg < pw; cg += 8) {
+                    T acc[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[j] = zero<T>();
+                    for (int kk = 0; kk < kw; ++kk) {
+                        const T a = Tt[kk * R + r];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (cg + j < pw) acc_fma(acc[j], a, Tt[kk * R + cg + j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int c = cg + j;
+                        if (c < pw && r >= c) P[c * R + r] = P[c * R + r] - acc_norm(acc[j]);
+                    }
+                }
+            }
+        }
+        for (int c = 0; c < pw; ++c) {
+            __syncthreads();
+            const T d = P[c * R + c];
+            const float dh = hi_of(d);
+            if (!(dh > 0.f)) return false;
+            dmin = fminf(dmin, dh);
+            dmax = fmaxf(dmax, dh);
+            const T ld = gsqrt(d);
+            const T il = from_f<T>(1.f) / ld;
+            __syncthreads();
+            for (int r = c + tid; r < R; r += nthr) P[c * R + r] = (r == c) ? ld : P[c * R + r] * il;
+            __syncthreads();
+            const int rest = pw - c - 1;
+            for (int idx = tid; idx < rest * R; idx += nthr) {
+                const int c2 = c + 1 + idx / R, r = idx % R;
+                if (r >= c2) P[c2 * R + r] = gfnma(P[c * R + r], P[c * R + c2], P[c2 * R + r]);
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < pw * R; idx += nthr) {
+            const int c = idx / R, r = idx - c * R;
+            if (r >= c) L[tri_off(p0 + c, n) + (r - c)] = P[idx];
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// X = L^-1 in place by row blocks of rb rows (rows above the block already hold X, rows
+// from the block down still hold L): stage the block's rows of L, then for every column
+// c left of the block X_Ic = -L_II^-1 sum_k L_Ik X_kc (thread per column, rb
+// accumulators, rb <= 16), and X_II = L_II^-1; results go straight to global memory.
+template <class T>
+__device__ void big_invert(T* L, int n, T* W, int rbmax)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int r0 = 0; r0 < n; r0 += rbmax) {
+        const int rb = min(rbmax, n - r0), cw = r0 + rb;
+        __syncthreads();
+        for (int idx = tid; idx < rb * cw; idx += nthr) {
+            const int c = idx / rb, r = idx - c * rb;
+            if (c <= r0 + r) W[r * n + c] = L[tri_off(c, n) + (r0 + r - c)];
+        }
+        __syncthreads();
+        for (int c = tid; c < cw; c += nthr) {
+            T z[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) z[r] = zero<T>();
+            if (c < r0) {
+                const T* xc = L + tri_off(c, n);  // X[k][c] at xc[k - c], k < r0
+                for (int k = c; k < r0; ++k) {
+                    const T x = xc[k - c];
+#pragma unroll
+                    for (int r = 0; r < 16; ++r)
+                        if (r < rb) acc_fma(z[r], W[r * n + k], x);
+                }
+#pragma unroll
+                for (int r = 0; r < 16; ++r) z[r] = -acc_norm(z[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 16; ++r)
+                    if (r0 + r == c) z[r] = from_f<T>(1.f);
+            }
+            // forward substitution with L_II
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                if (r < rb) {
+                    T s = z[r];
+#pragma unroll
+                    for (int q = 0; q < r; ++q) s = gfnma(W[r * n + r0 + q], z[q], s);
+                    z[r] = s / W[r * n + r0 + r];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (r < rb && r0 + r >= c) L[tri_off(c, n) + (r0 + r - c)] = z[r];
+        }
+    }
+    __syncthreads();
+}
+
 template <class T, bool TRI_SMEM>
 __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, const SmemPlan& P,
                             double* red, const T* nodes)
@@ -181,7 +309,13 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     // step k: A_ij -= A_ik A_jk / A_kk for k < j <= i, column k-1 scaled in the same
     // phase (it is not read by step k), one barrier per step.
     float dmin = 3.0e38f, dmax = 0.f;
-    {
+    T* W = reinterpret_cast<T*>(smem + P.off_work);
+    if (!TRI_SMEM) {
+        __syncthreads();
+        const bool ok = big_cholesky<T>(L, n, W, W + (int64_t)P.pb * n, P.pb, dmin, dmax);
+        if (!ok && tid == 0) s_fail = 1;
+        __syncthreads();
+    } else {
         const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
         T dprev = zero<T>();
         T rs_prev = zero<T>();
@@ -247,6 +381,7 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         return;
     }
 
+    if (!TRI_SMEM) big_invert<T>(L, n, W, P.rb);
     // ---- A4': X = L^-1 in place, right-looking elimination of L X = I -------------
     // step k: (a) row k is final: X_kc = B_kc / L_kk (c < k);
     //         (b) rows i > k: B_ic -= L_ik X_kc (c < k) and B_ik = -L_ik / L_kk.
@@ -254,7 +389,7 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     // it reads L_ik before the lane of column k overwrites it.  The diagonal keeps L_kk
     // until a last pass writes 1 / L_kk.  Two barriers per step; no thread runs a
     // serial dot product.
-    {
+    if (TRI_SMEM) {
         const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
         for (int k = 0; k < n; ++k) {
             __syncthreads();
