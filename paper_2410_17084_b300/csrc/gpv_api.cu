@@ -33,6 +33,7 @@ int cuda_fail(cudaError_t e)
 
 struct Bucket {
     int hi;        // largest n of the bucket
+    int nthr;      // CTA size
     int smem;      // dynamic shared memory of its launch
     int grid;      // persistent CTAs
     bool tri_smem; // factor in shared memory (else in the global workspace slice)
@@ -141,12 +142,13 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         hi_host[i] = B.hi;
         B.tri_smem = B.hi <= P.nmax_smem;
         // the workspace variant lays out its slice for max_points, whatever the bucket
+        B.nthr = solve_threads(B.hi, B.tri_smem);
         const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
-                                      tsize(kind), B.tri_smem);
+                                      tsize(kind), B.tri_smem, B.nthr);
         if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) return GPV_EINVAL;  // panels too thin
         B.smem = sp.total;
         int occ = 0;
-        CK(solve_occupancy(kind, B.tri_smem, B.smem, &occ));
+        CK(solve_occupancy(kind, B.tri_smem, B.nthr, B.smem, &occ));
         if (occ < 1) return GPV_EINVAL;
         B.grid = B.tri_smem ? h->sms * occ : h->gws_grid;
     }
@@ -313,12 +315,12 @@ static int create_impl(gp_voxels_t* h)
     {
         const PrecPlan& P = h->plan[PREC_F64];
         const int nsm = std::min(P.nmax_smem, c.max_points);
-        h->esc_smem_small = smem_plan(nsm, c.grid_side, h->Gp, 8, true).total;
+        h->esc_smem_small = smem_plan(nsm, c.grid_side, h->Gp, 8, true, solve_threads(nsm, true)).total;
         int occ = 0;
-        CK(solve_occupancy(PREC_F64, true, h->esc_smem_small, &occ));
+        CK(solve_occupancy(PREC_F64, true, solve_threads(nsm, true), h->esc_smem_small, &occ));
         h->esc_grid_small = h->sms * std::max(occ, 1);
-        h->esc_smem_big = smem_plan(c.max_points, c.grid_side, h->Gp, 8, false).total;
-        CK(solve_occupancy(PREC_F64, false, h->esc_smem_big, &occ));
+        h->esc_smem_big = smem_plan(c.max_points, c.grid_side, h->Gp, 8, false, 512).total;
+        CK(solve_occupancy(PREC_F64, false, 512, h->esc_smem_big, &occ));
         h->esc_grid_big = h->gws_grid;
     }
     if (c.hash_capacity > 0) {
@@ -398,11 +400,13 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             if (n < c.tau || n <= 0 || n > c.max_points) continue;
             a.work = h->d_ident + v;
             a.work_next = h->d_pl_next + v;
-            a.nmax = (int)((n + 7) / 8 * 8);
-            const bool sm = a.nmax <= P.nmax_smem;
-            if (!sm) a.nmax = c.max_points;
-            const int smem = smem_plan(a.nmax, c.grid_side, h->Gp, tsize(kind), sm).total;
-            CK(launch_solve(kind, sm, a, 1, smem, s));
+            // the launch configuration of the voxel's size bucket, one CTA
+            int b = P.nb - 1;
+            for (int k = 0; k < P.nb; ++k)
+                if (n <= P.b[k].hi) { b = k; break; }
+            const Bucket& B = P.b[b];
+            a.nmax = B.tri_smem ? B.hi : c.max_points;
+            CK(launch_solve(kind, B.tri_smem, B.nthr, a, 1, B.smem, s));
         }
         return GPV_OK;
     }
@@ -422,7 +426,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_count = x.d_bcount + b;
         a.work_next = x.d_next + b;
         a.nmax = B.tri_smem ? B.hi : c.max_points;
-        CK(launch_solve(kind, B.tri_smem, a, B.grid, B.smem, ss));
+        CK(launch_solve(kind, B.tri_smem, B.nthr, a, B.grid, B.smem, ss));
         used |= 1 << (si % kNumBuckets);
     }
     for (int i = 0; i < kNumBuckets; ++i)
@@ -439,13 +443,14 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_count = x.d_esc_count;
         a.work_next = x.d_next + P.nb;
         a.nmax = a.nmax_small_f64;
-        CK(launch_solve(PREC_F64, true, a, h->esc_grid_small, h->esc_smem_small, s));
+        CK(launch_solve(PREC_F64, true, solve_threads(a.nmax, true), a, h->esc_grid_small,
+                        h->esc_smem_small, s));
         if (c.max_points > a.nmax_small_f64) {
             a.work = x.d_esc_list + nvox;
             a.work_count = x.d_esc_count + 1;
             a.work_next = x.d_next + P.nb + 1;
             a.nmax = c.max_points;
-            CK(launch_solve(PREC_F64, false, a, h->esc_grid_big, h->esc_smem_big, s));
+            CK(launch_solve(PREC_F64, false, 512, a, h->esc_grid_big, h->esc_smem_big, s));
         }
     }
     return GPV_OK;

@@ -17,7 +17,7 @@ enum : uint32_t {
     VOX_TOO_LARGE = 16u,
 };
 
-constexpr int kThreads = 256;   // CTA size of the solve kernels
+constexpr int kThreads = 512;   // largest CTA size of the solve kernels
 constexpr int kRowBlk = 8;      // rows of L^-1 per register tile
 constexpr int kQryBlk = 4;      // queries per register tile
 constexpr int kMaxG = 32;       // largest query grid side
@@ -80,11 +80,12 @@ constexpr int kBigSmem = 216 * 1024;
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize, bool tri_in_smem)
+__host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize, bool tri_in_smem,
+                                              int nthr)
 {
     SmemPlan p;
     int nqg = (G * Gp) / kQryBlk;
-    int nrg = nqg >= kThreads ? 1 : kThreads / nqg;
+    int nrg = nqg >= nthr ? 1 : nthr / nqg;
     p.nqg = nqg;
     p.nrg = nrg;
     int o = 0;
@@ -122,14 +123,19 @@ __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize
 // Text of a CUDA error for gp_voxels_last_error() (gpv_api.cu)
 void gpv_record_cuda_error(cudaError_t e);
 
+// CTA size of a launch: small voxels are bound by the latency of their per-column
+// barriers and gain from two CTAs per SM; from 128 points on (and for the workspace
+// variant) shared memory allows one CTA per SM, which then gets 16 warps.
+inline int solve_threads(int nmax, bool tri_in_smem) { return (!tri_in_smem || nmax >= 128) ? 512 : 256; }
+
 // Launchers (gpv_solve.cu)
 cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, int32_t* bcount,
                             int32_t* bbase, int32_t* bcursor, int32_t* work, int32_t* next,
                             int32_t* esc_count, cudaStream_t s);
-cudaError_t launch_solve(int prec, bool tri_in_smem, const SolveArgs& a, int grid, int smem,
+cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& a, int grid, int smem,
                          cudaStream_t s);
 cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out);
-cudaError_t solve_occupancy(int prec, bool tri_in_smem, int smem, int* blocks_per_sm);
+cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm);
 cudaError_t launch_init(const float* mean, const float* var, const uint8_t* axis,
                         const float* centres, const float* sf2, const uint32_t* status,
                         int32_t nvox, float size, int G, int n_s, int n_r, int init_mode,

@@ -167,21 +167,23 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
                              scr + kOffEscCount, s)) != cudaSuccess)
         return fail(e);
     for (int b = nb - 1; b >= 0; --b) {
-        const int smem = smem_plan(bnd.hi[b], G, Gp, kind == PREC_F32 ? 4 : 8, true).total;
+        const int nt = solve_threads(bnd.hi[b], true);
+        const int smem = smem_plan(bnd.hi[b], G, Gp, kind == PREC_F32 ? 4 : 8, true, nt).total;
         int occ = 0;
-        if ((e = solve_occupancy(kind, true, smem, &occ)) != cudaSuccess) return fail(e);
+        if ((e = solve_occupancy(kind, true, nt, smem, &occ)) != cudaSuccess) return fail(e);
         if (occ < 1) return GPV_EINVAL;
         a.work = scr + kOffWork;
         a.work_base = scr + kOffBase + b;
         a.work_count = scr + kOffCount + b;
         a.work_next = scr + kOffNext + b;
         a.nmax = bnd.hi[b];
-        if ((e = launch_solve(kind, true, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
+        if ((e = launch_solve(kind, true, nt, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
     }
     if (kind == PREC_FF) {  // FP64 re-solve of the voxels that failed the conditioning check
-        const int smem = smem_plan(a.nmax_small_f64, G, Gp, 8, true).total;
+        const int nt = solve_threads(a.nmax_small_f64, true);
+        const int smem = smem_plan(a.nmax_small_f64, G, Gp, 8, true, nt).total;
         int occ = 0;
-        if ((e = solve_occupancy(PREC_F64, true, smem, &occ)) != cudaSuccess) return fail(e);
+        if ((e = solve_occupancy(PREC_F64, true, nt, smem, &occ)) != cudaSuccess) return fail(e);
         if (occ < 1) return GPV_EINVAL;
         a.escalate = 0;
         a.escalation_pass = 1;
@@ -190,7 +192,7 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
         a.work_count = scr + kOffEscCount;
         a.work_next = scr + kOffNext + nb;
         a.nmax = a.nmax_small_f64;
-        if ((e = launch_solve(PREC_F64, true, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
+        if ((e = launch_solve(PREC_F64, true, nt, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
     }
     return GPV_OK;
 }

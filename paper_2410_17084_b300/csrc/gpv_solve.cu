@@ -291,17 +291,32 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     const T sn2 = from_f<T>(sn2f);
     __syncthreads();
     {
-        // column c, rows r = c..n-1; one warp per column, lanes over rows
-        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
-        for (int c = wid; c < n; c += nw) {
-            const T xc = x1[c], yc = x2[c];
-            T* col = L + tri_off(c, n);
-            for (int r = c + lane; r < n; r += 32) {
-                T d1 = x1[r] - xc, d2 = x2[r] - yc;
-                T k = sf2 * gexp(nlam * (d1 * d1 + d2 * d2));
-                if (r == c) k = k + sn2;
-                col[r - c] = k;
+        // flattened lower triangle, two entries per thread in flight (the exponentials
+        // are long dependent chains); entry e of column c, row r: e = tri_off(c, n) + r - c
+        const int ntri = n * (n + 1) / 2;
+        for (int e0 = tid; e0 < ntri; e0 += 2 * nthr) {
+            const int e1 = min(e0 + nthr, ntri - 1);
+            int ce[2], re[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = u ? e1 : e0;
+                // column of entry e: the largest c with tri_off(c, n) <= e
+                const float b = 2.f * n + 1.f;
+                int c = (int)((b - sqrtf(b * b - 8.f * (float)e)) * 0.5f);
+                c = max(0, min(c, n - 1));
+                while (c > 0 && tri_off(c, n) > e) --c;
+                while (c + 1 < n && tri_off(c + 1, n) <= e) ++c;
+                ce[u] = c;
+                re[u] = c + (e - tri_off(c, n));
             }
+            const T d1a = x1[re[0]] - x1[ce[0]], d2a = x2[re[0]] - x2[ce[0]];
+            const T d1b = x1[re[1]] - x1[ce[1]], d2b = x2[re[1]] - x2[ce[1]];
+            T ka = sf2 * gexp(nlam * (d1a * d1a + d2a * d2a));
+            T kb = sf2 * gexp(nlam * (d1b * d1b + d2b * d2b));
+            if (re[0] == ce[0]) ka = ka + sn2;
+            if (re[1] == ce[1]) kb = kb + sn2;
+            L[e0] = ka;
+            if (e0 + nthr < ntri) L[e1] = kb;
         }
     }
 
@@ -339,7 +354,22 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             for (int j = k + 1 + wid; j < n; j += nw) {
                 const T s = colk[j - k] * inv_d;
                 T* colj = L + tri_off(j, n);
-                for (int i = j + lane; i < n; i += 32) colj[i - j] = gfnma(colk[i - k], s, colj[i - j]);
+                if (n - j <= 64) {  // short column: one update per lane
+                    for (int i = j + lane; i < n; i += 32) colj[i - j] = gfnma(colk[i - k], s, colj[i - j]);
+                    continue;
+                }
+                for (int i0 = j + lane; i0 < n; i0 += 128) {  // 4 independent updates
+                    T a[4], b[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = min(i0 + 32 * u, n - 1);
+                        a[u] = colk[i - k];
+                        b[u] = colj[i - j];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (i0 + 32 * u < n) colj[i0 + 32 * u - j] = gfnma(a[u], s, b[u]);
+                }
             }
             dprev = d;
             rs_prev = from_f<T>(1.f) / gsqrt(d);
@@ -402,9 +432,27 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             for (int i = k + 1 + wid; i < n; i += nw) {
                 const T m = L[tri_off(k, n) + (i - k)];
                 __syncwarp();
-                for (int c = lane; c <= k; c += 32) {
-                    T* p = L + tri_off(c, n) + (i - c);
-                    *p = (c == k) ? -(m * inv) : gfnma(m, L[tri_off(c, n) + (k - c)], *p);
+                if (k < 64) {  // short row: one update per lane
+                    for (int c = lane; c <= k; c += 32) {
+                        T* p = L + tri_off(c, n) + (i - c);
+                        *p = (c == k) ? -(m * inv) : gfnma(m, L[tri_off(c, n) + (k - c)], *p);
+                    }
+                    continue;
+                }
+                for (int c0 = lane; c0 <= k; c0 += 128) {  // 4 independent updates
+                    T x[4], b[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = min(c0 + 32 * u, k);
+                        x[u] = L[tri_off(c, n) + (k - c)];
+                        b[u] = L[tri_off(c, n) + (i - c)];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = c0 + 32 * u;
+                        if (c <= k)
+                            L[tri_off(c, n) + (i - c)] = (c == k) ? -(m * inv) : gfnma(m, x[u], b[u]);
+                    }
                 }
             }
         }
@@ -417,20 +465,30 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     }
 
     // ---- A5: alpha = X^T (X (f - m)) ----------------------------------------------
-    for (int j = tid; j < n; j += nthr) {
-        T s = zero<T>();
-        for (int i = 0; i <= j; ++i) s = gfma(L[tri_off(i, n) + (j - i)], fv[i], s);
-        tmp[j] = s;
+    for (int j = tid; j < n; j += nthr) {  // four partial sums in flight
+        T s4[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
+        int i = 0;
+        for (; i + 3 <= j; i += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc_fma(s4[u], L[tri_off(i + u, n) + (j - i - u)], fv[i + u]);
+        for (; i <= j; ++i) acc_fma(s4[0], L[tri_off(i, n) + (j - i)], fv[i]);
+        tmp[j] = (acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3]));
     }
     // ---- A6: separable cross-covariance factors --------------------------------------
     {
-        for (int t = tid; t < n * G; t += nthr) {
-            const int i = t / G, u = t - i * G;
-            const T node = nodes[u];
-            T d1 = x1[i] - node;
-            T d2 = x2[i] - node;
-            fa[i * G + u] = sf2 * gexp(nlam * (d1 * d1));
-            fb[i * Gp + u] = gexp(nlam * (d2 * d2));
+        for (int t0 = tid; t0 < n * G; t0 += 2 * nthr) {  // four exponentials in flight
+            const int t1 = min(t0 + nthr, n * G - 1);
+            const int i0 = t0 / G, u0 = t0 - i0 * G, i1 = t1 / G, u1 = t1 - i1 * G;
+            const T da0 = x1[i0] - nodes[u0], db0 = x2[i0] - nodes[u0];
+            const T da1 = x1[i1] - nodes[u1], db1 = x2[i1] - nodes[u1];
+            const T ea0 = gexp(nlam * (da0 * da0)), eb0 = gexp(nlam * (db0 * db0));
+            const T ea1 = gexp(nlam * (da1 * da1)), eb1 = gexp(nlam * (db1 * db1));
+            fa[i0 * G + u0] = sf2 * ea0;
+            fb[i0 * Gp + u0] = eb0;
+            if (t0 + nthr < n * G) {
+                fa[i1 * G + u1] = sf2 * ea1;
+                fb[i1 * Gp + u1] = eb1;
+            }
         }
         for (int t = tid; t < n * (Gp - G); t += nthr) {
             const int i = t / (Gp - G), u = G + (t - i * (Gp - G));
@@ -438,10 +496,15 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         }
     }
     __syncthreads();
-    for (int i = tid; i < n; i += nthr) {
-        T s = zero<T>();
-        for (int j = i; j < n; ++j) s = gfma(L[tri_off(i, n) + (j - i)], tmp[j], s);
-        al[i] = s;
+    for (int i = tid; i < n; i += nthr) {  // four partial sums in flight
+        T s4[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
+        const T* col = L + tri_off(i, n) - i;
+        int j = i;
+        for (; j + 3 < n; j += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc_fma(s4[u], col[j + u], tmp[j + u]);
+        for (; j < n; ++j) acc_fma(s4[0], col[j], tmp[j]);
+        al[i] = (acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3]));
     }
 
     // ---- A8: |X k_q|^2 by register-tiled contraction ------------------------------
@@ -501,8 +564,14 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     const bool want_init = A.pos != nullptr;
     for (int q = tid; q < GG; q += nthr) {
         const int u = q / G, vv = q - u * G;
-        T mu = m;
-        for (int i = 0; i < n; ++i) mu = gfma(al[i] * fa[i * G + u], fb[i * Gp + vv], mu);
+        T s4[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
+        int i = 0;
+        for (; i + 3 < n; i += 4)
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                acc_fma(s4[w], al[i + w] * fa[(i + w) * G + u], fb[(i + w) * Gp + vv]);
+        for (; i < n; ++i) acc_fma(s4[0], al[i] * fa[i * G + u], fb[i * Gp + vv]);
+        const T mu = m + ((acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3])));
         T nr = zero<T>();
         for (int g = 0; g < P.nrg; ++g) nr = nr + part[g * (G * Gp) + u * Gp + vv];
         T var = sf2 - nr;
@@ -530,14 +599,14 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     __syncthreads();
 }
 
-template <class T, bool TRI_SMEM>
-__global__ void __launch_bounds__(kThreads) k_solve(SolveArgs A)
+template <class T, bool TRI_SMEM, int NT>
+__global__ void __launch_bounds__(NT) k_solve(SolveArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[6 * 32];
     __shared__ T nodes[kMaxG];
     __shared__ int s_v;
-    const SmemPlan P = smem_plan(A.nmax, A.G, A.Gp, (int)sizeof(T), TRI_SMEM);
+    const SmemPlan P = smem_plan(A.nmax, A.G, A.Gp, (int)sizeof(T), TRI_SMEM, NT);
     // query grid nodes -s/2 + (u + 1/2) s / G, formed once in FP64 and rounded to T
     if (threadIdx.x < A.G)
         nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
@@ -643,18 +712,19 @@ cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, in
 // The dynamic shared-memory limit of every instantiation is raised once, when the
 // handle plans its launches (solve_occupancy), so launches stay capturable.
 template <class T, bool S>
-static cudaError_t launch_t(const SolveArgs& a, int grid, int smem, cudaStream_t s)
+static cudaError_t launch_t(int nthr, const SolveArgs& a, int grid, int smem, cudaStream_t s)
 {
-    k_solve<T, S><<<grid, kThreads, smem, s>>>(a);
+    if (nthr == 512) k_solve<T, S, 512><<<grid, 512, smem, s>>>(a);
+    else k_solve<T, S, 256><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_solve(int prec, bool tri_in_smem, const SolveArgs& a, int grid, int smem,
-                         cudaStream_t s)
+cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& a, int grid,
+                         int smem, cudaStream_t s)
 {
-    if (prec == PREC_F32) return tri_in_smem ? launch_t<float, true>(a, grid, smem, s) : launch_t<float, false>(a, grid, smem, s);
-    if (prec == PREC_F64) return tri_in_smem ? launch_t<double, true>(a, grid, smem, s) : launch_t<double, false>(a, grid, smem, s);
-    return tri_in_smem ? launch_t<ff, true>(a, grid, smem, s) : launch_t<ff, false>(a, grid, smem, s);
+    if (prec == PREC_F32) return tri_in_smem ? launch_t<float, true>(nthr, a, grid, smem, s) : launch_t<float, false>(nthr, a, grid, smem, s);
+    if (prec == PREC_F64) return tri_in_smem ? launch_t<double, true>(nthr, a, grid, smem, s) : launch_t<double, false>(nthr, a, grid, smem, s);
+    return tri_in_smem ? launch_t<ff, true>(nthr, a, grid, smem, s) : launch_t<ff, false>(nthr, a, grid, smem, s);
 }
 
 static int tsize_of(int prec) { return prec == PREC_F32 ? 4 : 8; }
@@ -666,22 +736,28 @@ cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const int static_bytes = 6 * 32 * 8 + 64;
+    const int static_bytes = 6 * 32 * 8 + 32 * 8 + 64;
     int best = 0;
     for (int n = 8; n <= 1024; n += 8) {
-        SmemPlan p = smem_plan(n, G, Gp, tsize_of(prec), true);
+        SmemPlan p = smem_plan(n, G, Gp, tsize_of(prec), true, solve_threads(n, true));
         if (p.total + static_bytes <= optin) best = n;
     }
     *nmax_out = best;
     return cudaSuccess;
 }
 
-cudaError_t solve_occupancy(int prec, bool tri_in_smem, int smem, int* blocks_per_sm)
+template <class T, bool S>
+static const void* kfun(int nthr)
+{
+    return nthr == 512 ? (const void*)k_solve<T, S, 512> : (const void*)k_solve<T, S, 256>;
+}
+
+cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm)
 {
     const void* f;
-    if (prec == PREC_F32) f = tri_in_smem ? (const void*)k_solve<float, true> : (const void*)k_solve<float, false>;
-    else if (prec == PREC_F64) f = tri_in_smem ? (const void*)k_solve<double, true> : (const void*)k_solve<double, false>;
-    else f = tri_in_smem ? (const void*)k_solve<ff, true> : (const void*)k_solve<ff, false>;
+    if (prec == PREC_F32) f = tri_in_smem ? kfun<float, true>(nthr) : kfun<float, false>(nthr);
+    else if (prec == PREC_F64) f = tri_in_smem ? kfun<double, true>(nthr) : kfun<double, false>(nthr);
+    else f = tri_in_smem ? kfun<ff, true>(nthr) : kfun<ff, false>(nthr);
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -694,7 +770,7 @@ cudaError_t solve_occupancy(int prec, bool tri_in_smem, int smem, int* blocks_pe
                              optin - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return e;
     if (smem > optin - (int)fa.sharedSizeBytes) { *blocks_per_sm = 0; return cudaSuccess; }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, nthr, smem);
 }
 
 // ---- standalone Gaussian initialisation from FP32 predictions ---------------------
