@@ -101,9 +101,38 @@ def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-# FP32 instructions per float-float multiply-add (TwoProduct with two correction FMAs and
-# a fast renormalisation = 7, accurate float-float addition = 20)
-FF_OPS_PER_FMA = 27
+# FP32 instructions per float-float multiply-add in the dominant loop (the contraction
+# behind diag Sigma*): TwoProduct (2), two cross-term FMAs (2), TwoSum into the running
+# sum (6), two additions into the error word (2)
+FF_OPS_PER_FMA = 12
+
+
+def ff_peak_tflops(sm_mhz: float) -> float:
+    """Float-float FLOP/s the FP32 pipes can sustain: FP32 instructions per second /
+    FF_OPS_PER_FMA float-float multiply-adds, 2 flops each."""
+    return 148 * 128 * sm_mhz * 1e6 / FF_OPS_PER_FMA * 2 / 1e12
+
+
+def traffic_from_profiles(nvox_step: int):
+    """DRAM bytes per step of the solve kernels from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2410_17084_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    sha = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "solve_ff_quadric_traffic.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_voxel:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1)) * nvox_step
 
 
 def run_reference(args, rank, world):
@@ -166,6 +195,100 @@ def cpu_baseline_leg(b, budget_s=12.0) -> dict:
     return {"value": k / dt, "unit": "voxel solves/s", "cores": ncpu, "kind": "oracle",
             "sample": f"first {k} of {b.nvox} voxels of the workload (GPR + Gaussian init)",
             "seconds": dt}
+
+
+def run_extras(b, d, stream, timed) -> dict:
+    """Secondary legs: plain FP32 batched, the plain one-voxel-per-launch FP32 baseline,
+    the mixed-precision escalation workload (sample), the 1M-voxel stress workload as one
+    CUDA-graph replay, and serving at 10 Hz."""
+    import torch
+    from paper_2410_17084_b300 import gp_voxels as gv, serve, synth
+    ex = {}
+
+    def solve_leg(batch, dev, prec, steps=3, warmup=3, graph=False, init=True):
+        cfg = gv.gp_voxels_config_default(voxel_size=batch.size, grid_side=batch.G,
+                                          n_s=batch.n_s, n_r=batch.n_r, tau=batch.tau,
+                                          max_points=int(max(256, batch.counts.max())),
+                                          max_voxels=batch.nvox, precision=prec)
+        g = gv.GpVoxels(cfg)
+        o = g.outputs(batch.nvox, "cuda", init=init)
+        # queued on the current stream, so that a graph capture records it
+        f = lambda: g.solve_csr(dev["xyz"], dev["offsets"], dev["centres"], dev["lam"],
+                                dev["sf2"], dev["sn2"], out=o, init=init)
+        if graph:
+            gr = gv.capture_graph(f)
+            f = gr.replay
+        ms = timed(f, steps, warmup)
+        st = o["status"].cpu().numpy()
+        g.close()
+        t = sum(ms) / len(ms)
+        return {"value": batch.nvox / (t * 1e-3), "unit": "voxel solves/s", "ms_per_step": t,
+                "predicted_pts_per_s": batch.nvox * batch.G * batch.G / (t * 1e-3),
+                "escalated": int(((st & gv.VOX_ESCALATED) != 0).sum())}
+
+    try:
+        ex["fp32_batched"] = solve_leg(b, d, gv.PREC_FP32)
+        nsub = 5000
+        bs = b.subset(np.arange(nsub))
+        ds = gv.batch_to_device(bs)
+        gsub = gv.GpVoxels(gv.gp_voxels_config_default(
+            voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau, max_points=256,
+            max_voxels=nsub, precision=gv.PREC_FP32))
+        osub = gsub.outputs(nsub, "cuda", init=True)
+        mpl = timed(lambda: gsub.solve_csr(ds["xyz"], ds["offsets"], ds["centres"], ds["lam"],
+                                           ds["sf2"], ds["sn2"], out=osub, init=True,
+                                           one_per_launch=True, stream=stream), 2, 1)
+        gsub.close()
+        tpl = sum(mpl) / len(mpl)
+        ex["fp32_one_voxel_per_launch"] = {"value": nsub / (tpl * 1e-3), "unit": "voxel solves/s",
+                                           "sample_voxels": nsub}
+    except Exception as e:  # an extra must not lose the headline
+        ex["fp32_error"] = repr(e)
+    try:
+        c3 = synth.mixed_batch(20000)
+        d3 = gv.batch_to_device(c3)
+        ex["mixed200k_sample"] = {
+            "workload": "first 20,000 of the 200,000-voxel escalation workload (counts "
+                        "power-law on [32,512], 10% collinear voxels, G = 32)",
+            "mixed": solve_leg(c3, d3, gv.PREC_MIXED, steps=2, warmup=1),
+            "fp32": solve_leg(c3, d3, gv.PREC_FP32, steps=2, warmup=1)}
+        del d3
+    except Exception as e:
+        ex["mixed200k_error"] = repr(e)
+    try:
+        c5 = synth.stress_batch(1000000)
+        d5 = gv.batch_to_device(c5)
+        ex["stress1m"] = {
+            "workload": "1,000,000 voxels, counts power-law on [4,1024], G = 9, fused "
+                        "Gaussian init, one CUDA-graph replay per step",
+            "fp32_graph": solve_leg(c5, d5, gv.PREC_FP32, steps=1, warmup=1, graph=True)}
+        s5 = c5.subset(np.arange(200000))
+        del d5
+        ds5 = gv.batch_to_device(s5)
+        ex["stress1m"]["mixed_graph_first200k"] = solve_leg(s5, ds5, gv.PREC_MIXED, steps=1,
+                                                            warmup=1, graph=True)
+        del ds5
+    except Exception as e:
+        ex["stress1m_error"] = repr(e)
+    try:
+        scene = synth.lidar_scene()
+        nsc = 100
+        scans = [synth.lidar_scan(scene, k) for k in range(nsc)]
+        srv = serve.Server(serve.serving_config())
+        srv.run(scans[:3], realtime=False)  # first-use set-up of the kernels
+        srv2 = serve.Server(serve.serving_config())
+        lat, wall, _ = srv2.run(scans, arrivals=scene.arrivals[:nsc], realtime=True)
+        srv.close()
+        srv2.close()
+        ex["serving"] = {
+            "workload": f"{nsc} synthetic 64x1024 LiDAR scans, Poisson arrivals at 10 Hz, "
+                        "0.5 m voxels, 256-point buckets, G = 9, mixed precision + init",
+            "p50_ms": float(np.percentile(lat * 1e3, 50)),
+            "p99_ms": float(np.percentile(lat * 1e3, 99)),
+            "max_ms": float(lat.max() * 1e3), "scans_per_s": nsc / wall}
+    except Exception as e:
+        ex["serving_error"] = repr(e)
+    return ex
 
 
 def main():
@@ -244,6 +367,7 @@ def main():
     value = world * b.nvox / (t_step * 1e-3)
     st = out["status"].cpu().numpy()
     n_esc = int(((st & gv.VOX_ESCALATED) != 0).sum())
+    launches = gv.gp_voxels_last_launches(g.h)
 
     # ---- e2e: host buffers in, host buffers out, through the C ABI ------------------
     pin = {k: torch.from_numpy(getattr(b, k)).pin_memory() for k in
@@ -264,41 +388,9 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
-        # plain FP32 batched and the plain one-voxel-per-launch FP32 baseline
-        cfg32 = gv.gp_voxels_config_default(voxel_size=b.size, grid_side=G, n_s=b.n_s,
-                                            n_r=b.n_r, tau=b.tau, max_points=256,
-                                            max_voxels=b.nvox, precision=gv.PREC_FP32)
-        g32 = gv.GpVoxels(cfg32)
-        o32 = g32.outputs(b.nvox, "cuda", init=True)
-        m32 = timed(lambda: step(g32, o32), 3, 3)
-        t32 = sum(m32) / len(m32)
-        extras["fp32_batched"] = {"value": b.nvox / (t32 * 1e-3), "ms_per_step": t32}
-        # one voxel per launch: time a 5,000-voxel prefix, scaled per voxel
-        nsub = 5000
-        bs = b.subset(np.arange(nsub))
-        ds = gv.batch_to_device(bs)
-        gsub = gv.GpVoxels(gv.gp_voxels_config_default(
-            voxel_size=b.size, grid_side=G, n_s=b.n_s, n_r=b.n_r, tau=b.tau, max_points=256,
-            max_voxels=nsub, precision=gv.PREC_FP32))
-        osub = gsub.outputs(nsub, "cuda", init=True)
-
-        def one_per_launch():
-            gv.gp_voxels_solve_csr(gsub.h, ds["xyz"], ds["offsets"], nsub, ds["centres"],
-                                   ds["lam"], ds["sf2"], ds["sn2"], osub["axis"], osub["mean"],
-                                   osub["var"], osub["status"], osub["pos"], osub["scale"],
-                                   osub["quat"], gv.SOLVE_ONE_PER_LAUNCH, stream)
-        mpl = timed(one_per_launch, 2, 1)
-        tpl = sum(mpl) / len(mpl)
-        extras["fp32_one_voxel_per_launch"] = {"value": nsub / (tpl * 1e-3),
-                                               "sample_voxels": nsub}
-        extras["mixed_vs_one_per_launch"] = value / world / extras["fp32_one_voxel_per_launch"]["value"]
-        g32.close()
-        gsub.close()
-
+        extras = run_extras(b, d, stream, timed)
     clocks = clk.summary()
-    sm_mhz = clocks.get("sm_mhz") or 2032.0
-    peak_fp32 = fp32_alu_peak_tflops(2032.0)
-    peak_ff = peak_fp32 * 2.0 / FF_OPS_PER_FMA
+    peak_ff = ff_peak_tflops(2032.0)
     achieved = flops / (t_step * 1e-3) / 1e12
     line = {
         "metric": METRIC,
@@ -319,16 +411,21 @@ def main():
                    "parallelism": f"independent batches per GPU x{world}"},
         "predicted_pts_per_s": value * G * G,
         "escalated_voxels": n_esc,
-        "gpu_launches": None,
+        "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ff, "unit": "TFLOP/s",
-                     "frac": achieved / peak_ff, "traffic": None,
-                     "peak_note": "float-float FMA rate = FP32 ALU peak (148 SMs x 128 lanes x "
-                                  "2 x 2032 MHz) x 2 / 27 FP32 ops per float-float FMA"},
+                     "frac": achieved / peak_ff, "traffic": traffic_from_profiles(b.nvox),
+                     "peak_note": "float-float FLOP/s of the FP32 pipes: 148 SMs x 128 lanes x "
+                                  "2032 MHz FP32 instructions/s / 12 per float-float "
+                                  "multiply-add x 2 flops (derived from unit counts and the "
+                                  "maximum clock, not measured)"},
         "e2e": {"value": world * b.nvox / (t_e2e * 1e-3), "unit": "voxel solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clocks,
     }
     line.update(extras)
+    if "fp32_one_voxel_per_launch" in extras:
+        line["mixed_vs_fp32_one_voxel_per_launch"] = (
+            value / world / extras["fp32_one_voxel_per_launch"]["value"])
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg(b)
     if rank == 0:

@@ -239,6 +239,10 @@ GPV_API int gp_voxels_solve_csr_noalloc(const gp_voxels_config* cfg, const float
  * the voxel store).  Errors: GPV_EINVAL. */
 GPV_API int gp_voxels_query_sizes(const gp_voxels_config* cfg, size_t* bytes_out);
 
+/* Number of CUDA kernels the last gp_voxels_solve_csr / gp_voxels_solve call of this
+ * handle queued (a diagnostic; the paper has no counterpart).  Errors: GPV_EINVAL. */
+GPV_API int gp_voxels_last_launches(const gp_voxels_t* h, int32_t* h_kernels);
+
 /* Static text of a gpv_status code. */
 GPV_API const char* gp_voxels_strerror(int status);
 

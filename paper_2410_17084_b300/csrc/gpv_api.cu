@@ -79,6 +79,7 @@ struct gp_voxels {
     int esc_grid_small = 0, esc_smem_small = 0, esc_grid_big = 0, esc_smem_big = 0;
     size_t bytes = 0;
     gpv_store* store = nullptr;
+    int last_launches = 0;          // kernels queued by the last solve call
 };
 
 static int prec_kind(int precision)
@@ -384,6 +385,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     a.nmax_small_f64 = std::min(h->plan[PREC_F64].nmax_smem, c.max_points);
     CK(launch_classify(a, P.d_hi, P.nb, x.d_bcount, x.d_bbase, x.d_bcursor, x.d_work,
                        x.d_next, x.d_esc_count, s));
+    h->last_launches = 3;  // classify, bucket offsets, scatter
     if (nvox == 0) return GPV_OK;
 
     if (flags & GPV_SOLVE_ONE_PER_LAUNCH) {
@@ -407,6 +409,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             const Bucket& B = P.b[b];
             a.nmax = B.tri_smem ? B.hi : c.max_points;
             CK(launch_solve(kind, B.tri_smem, B.nthr, a, 1, B.smem, s));
+            ++h->last_launches;
         }
         return GPV_OK;
     }
@@ -427,6 +430,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_next = x.d_next + b;
         a.nmax = B.tri_smem ? B.hi : c.max_points;
         CK(launch_solve(kind, B.tri_smem, B.nthr, a, B.grid, B.smem, ss));
+        ++h->last_launches;
         used |= 1 << (si % kNumBuckets);
     }
     for (int i = 0; i < kNumBuckets; ++i)
@@ -445,12 +449,14 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.nmax = a.nmax_small_f64;
         CK(launch_solve(PREC_F64, true, solve_threads(a.nmax, true), a, h->esc_grid_small,
                         h->esc_smem_small, s));
+        ++h->last_launches;
         if (c.max_points > a.nmax_small_f64) {
             a.work = x.d_esc_list + nvox;
             a.work_count = x.d_esc_count + 1;
             a.work_next = x.d_next + P.nb + 1;
             a.nmax = c.max_points;
             CK(launch_solve(PREC_F64, false, 512, a, h->esc_grid_big, h->esc_smem_big, s));
+            ++h->last_launches;
         }
     }
     return GPV_OK;
@@ -537,6 +543,7 @@ extern "C" int gp_voxels_solve(gp_voxels_t* h, int32_t slot, uint8_t* d_axis, fl
     if (rc != GPV_OK) return rc;
     CK(store_or_flags(st, slot, d_status, s));
     CK(store_copy_rows(st, slot, d_keys, d_centres, s));
+    h->last_launches += 1 + ((d_keys || d_centres) ? 1 : 0);
     return GPV_OK;
 }
 
@@ -576,6 +583,13 @@ extern "C" int gp_voxels_store_voxels(gp_voxels_t* h, int64_t* h_voxels)
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(&n, h->store->nvox, sizeof(n), cudaMemcpyDeviceToHost));
     *h_voxels = n;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_last_launches(const gp_voxels_t* h, int32_t* h_kernels)
+{
+    if (!h || !h_kernels) return GPV_EINVAL;
+    *h_kernels = h->last_launches;
     return GPV_OK;
 }
 

@@ -25,6 +25,7 @@ EXPORTED = [
     "gp_voxels_init_gaussians", "gp_voxels_query_sizes", "gp_voxels_strerror",
     "gp_voxels_last_error", "gp_voxels_insert_scan", "gp_voxels_solve", "gp_voxels_scan_info",
     "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
+    "gp_voxels_last_launches",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -93,6 +94,7 @@ def lib() -> ctypes.CDLL:
         L.gp_voxels_solve_csr_noalloc.argtypes = [ctypes.POINTER(gp_voxels_config), P, P,
                                                   ctypes.c_int32, P, P, P, P, P, P, P, P, P,
                                                   P, P, P]
+        L.gp_voxels_last_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -213,6 +215,12 @@ def gp_voxels_release_scan(h, slot, stream=None) -> None:
     _check("gp_voxels_release_scan", lib().gp_voxels_release_scan(h, int(slot), _stream(stream)))
 
 
+def gp_voxels_last_launches(h) -> int:
+    n = ctypes.c_int32()
+    _check("gp_voxels_last_launches", lib().gp_voxels_last_launches(h, ctypes.byref(n)))
+    return n.value
+
+
 def gp_voxels_store_voxels(h) -> int:
     n = ctypes.c_int64()
     _check("gp_voxels_store_voxels", lib().gp_voxels_store_voxels(h, ctypes.byref(n)))
@@ -288,6 +296,24 @@ class GpVoxels:
         gp_voxels_init_gaussians(self.h, nvox, axis, centres, sf2, mean, var, status, out["pos"],
                                  out["scale"], out["quat"], stream)
         return out
+
+
+def capture_graph(fn, warmup: int = 1):
+    """Capture the GPU work that ``fn()`` queues on the current stream (solve calls
+    queue only capturable operations: kernels, memsets, event fork/join) into a CUDA
+    graph; returns the graph (``graph.replay()`` re-runs it)."""
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g
 
 
 def batch_to_device(b, device="cuda") -> dict:

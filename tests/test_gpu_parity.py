@@ -262,3 +262,27 @@ def test_full_size_sampled(gpv, oracle):
     sub_out = {k: out[k][idx] for k in ("axis", "mean", "var", "status")}
     _check(gpv, sub, sub_out, oracle, MEAN_TOL, VAR_TOL, "quadric50k sampled")
     assert np.all(np.isfinite(out["pos"])) and np.all(out["scale"] >= 0)
+
+
+def test_graph_replay_equals_direct_call(gpv):
+    """The batched solve (size buckets on forked streams, FP64 escalation pass) is
+    captured into a CUDA graph; a replay gives the direct call's outputs bit for bit."""
+    import torch
+    from paper_2410_17084_b300 import synth
+    b = synth.mixed_batch(600, seed=41)
+    g = gpv.GpVoxels(_cfg(gpv, b, 1))
+    d = gpv.batch_to_device(b)
+    ref = g.solve_csr(d["xyz"], d["offsets"], d["centres"], d["lam"], d["sf2"], d["sn2"], init=True)
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    out = g.outputs(b.nvox, "cuda", init=True)
+    graph = gpv.capture_graph(lambda: g.solve_csr(d["xyz"], d["offsets"], d["centres"], d["lam"],
+                                                  d["sf2"], d["sn2"], out=out, init=True))
+    for v in out.values():
+        v.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for k, v in out.items():
+        assert np.array_equal(v.cpu().numpy(), ref[k]), k
+    assert ((ref["status"] & 2) != 0).any()  # the escalation pass ran inside the graph
+    g.close()
