@@ -239,6 +239,20 @@ GPV_API int gp_voxels_solve_csr_noalloc(const gp_voxels_config* cfg, const float
  * the voxel store).  Errors: GPV_EINVAL. */
 GPV_API int gp_voxels_query_sizes(const gp_voxels_config* cfg, size_t* bytes_out);
 
+/* Autotuner of the batched solve (the paper has no counterpart; its batch is a library
+ * call): runs every size bucket of this batch with each candidate CTA size (256 and 512
+ * threads; persistent grids sized by occupancy) and keeps the fastest per bucket in the
+ * handle for later solves of any batch.  Inputs and outputs as gp_voxels_solve_csr (the
+ * outputs are overwritten with scratch results; the FP64 escalation is not run).
+ * Synchronises `stream`.  *h_changed = buckets whose choice changed.
+ * Errors: GPV_EINVAL, GPV_ECUDA. */
+GPV_API int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets,
+                               int32_t nvox, const float* d_centres, const float* d_lambda,
+                               const float* d_sf2, const float* d_sn2, uint8_t* d_axis,
+                               float* d_mean, float* d_var, uint32_t* d_status, float* d_pos,
+                               float* d_scale, float* d_quat, gpv_stream_t stream,
+                               int32_t* h_changed);
+
 /* Number of CUDA kernels the last gp_voxels_solve_csr / gp_voxels_solve call of this
  * handle queued (a diagnostic; the paper has no counterpart).  Errors: GPV_EINVAL. */
 GPV_API int gp_voxels_last_launches(const gp_voxels_t* h, int32_t* h_kernels);

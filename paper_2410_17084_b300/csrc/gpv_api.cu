@@ -359,16 +359,14 @@ extern "C" int gp_voxels_destroy(gp_voxels_t* h)
 }
 
 // Shared by the CSR entry and the serving solve: queue one batched solve.
-static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
+static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
                            const int64_t* d_offsets, int32_t nvox, const int32_t* d_nvox,
                            const float* d_centres, const float* d_lambda, const float* d_sf2,
                            const float* d_sn2, uint8_t* d_axis, float* d_mean, float* d_var,
-                           uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat,
-                           uint32_t flags, cudaStream_t s)
+                           uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat)
 {
     const gp_voxels_config& c = h->cfg;
     const int kind = prec_kind(c.precision);
-    const PrecPlan& P = h->plan[kind];
     SolveArgs a;
     memset(&a, 0, sizeof(a));
     a.xyz = d_xyz; a.offsets = d_offsets; a.centres = d_centres;
@@ -383,6 +381,21 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     a.gws = x.d_gws; a.gws_stride = h->gws_stride;
     a.max_points = c.max_points;
     a.nmax_small_f64 = std::min(h->plan[PREC_F64].nmax_smem, c.max_points);
+    return a;
+}
+
+static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
+                           const int64_t* d_offsets, int32_t nvox, const int32_t* d_nvox,
+                           const float* d_centres, const float* d_lambda, const float* d_sf2,
+                           const float* d_sn2, uint8_t* d_axis, float* d_mean, float* d_var,
+                           uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat,
+                           uint32_t flags, cudaStream_t s)
+{
+    const gp_voxels_config& c = h->cfg;
+    const int kind = prec_kind(c.precision);
+    const PrecPlan& P = h->plan[kind];
+    SolveArgs a = make_args(h, x, d_xyz, d_offsets, nvox, d_nvox, d_centres, d_lambda, d_sf2,
+                            d_sn2, d_axis, d_mean, d_var, d_status, d_pos, d_scale, d_quat);
     CK(launch_classify(a, P.d_hi, P.nb, x.d_bcount, x.d_bbase, x.d_bcursor, x.d_work,
                        x.d_next, x.d_esc_count, s));
     h->last_launches = 3;  // classify, bucket offsets, scatter
@@ -583,6 +596,76 @@ extern "C" int gp_voxels_store_voxels(gp_voxels_t* h, int64_t* h_voxels)
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(&n, h->store->nvox, sizeof(n), cudaMemcpyDeviceToHost));
     *h_voxels = n;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets,
+                                  int32_t nvox, const float* d_centres, const float* d_lambda,
+                                  const float* d_sf2, const float* d_sn2, uint8_t* d_axis,
+                                  float* d_mean, float* d_var, uint32_t* d_status, float* d_pos,
+                                  float* d_scale, float* d_quat, gpv_stream_t stream,
+                                  int32_t* h_changed)
+{
+    if (!h || nvox <= 0 || nvox > h->cfg.max_voxels || !h_changed) return GPV_EINVAL;
+    if (!d_xyz || !d_offsets || !d_centres || !d_lambda || !d_sf2 || !d_sn2 || !d_axis ||
+        !d_mean || !d_var || !d_status)
+        return GPV_EINVAL;
+    const bool any_init = d_pos || d_scale || d_quat;
+    if (any_init && !(d_pos && d_scale && d_quat)) return GPV_EINVAL;
+    const gp_voxels_config& c = h->cfg;
+    const int kind = prec_kind(c.precision);
+    PrecPlan& P = h->plan[kind];
+    SolveCtx& x = h->main;
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveArgs a = make_args(h, x, d_xyz, d_offsets, nvox, nullptr, d_centres, d_lambda, d_sf2,
+                            d_sn2, d_axis, d_mean, d_var, d_status, d_pos, d_scale, d_quat);
+    a.escalate = 0;  // time every voxel in this precision
+    CK(launch_classify(a, P.d_hi, P.nb, x.d_bcount, x.d_bbase, x.d_bcursor, x.d_work, x.d_next,
+                       x.d_esc_count, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int changed = 0;
+    const int cand[2] = {256, 512};
+    for (int b = 0; b < P.nb; ++b) {
+        Bucket& B = P.b[b];
+        float best_ms = 3.0e38f;
+        int best = B.nthr, best_smem = B.smem, best_grid = B.grid;
+        for (int ci = 0; ci < 2; ++ci) {
+            const int nt = cand[ci];
+            const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
+                                          tsize(kind), B.tri_smem, nt);
+            if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) continue;
+            int occ = 0;
+            CK(solve_occupancy(kind, B.tri_smem, nt, sp.total, &occ));
+            if (occ < 1) continue;
+            const int grid = B.tri_smem ? h->sms * occ : h->gws_grid;
+            a.work = x.d_work;
+            a.work_base = x.d_bbase + b;
+            a.work_count = x.d_bcount + b;
+            a.work_next = x.d_next + b;
+            a.nmax = B.tri_smem ? B.hi : c.max_points;
+            float ms = 3.0e38f;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel
+                CK(cudaMemsetAsync(x.d_next + b, 0, sizeof(int32_t), s));
+                CK(cudaEventRecord(e0, s));
+                CK(launch_solve(kind, B.tri_smem, nt, a, grid, sp.total, s));
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                ms = std::min(ms, t);
+            }
+            if (ms < best_ms) { best_ms = ms; best = nt; best_smem = sp.total; best_grid = grid; }
+        }
+        if (best != B.nthr) ++changed;
+        B.nthr = best;
+        B.smem = best_smem;
+        B.grid = best_grid;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *h_changed = changed;
     return GPV_OK;
 }
 

@@ -123,14 +123,28 @@ template <> __device__ __forceinline__ ff diff_f<ff>(float a, float b) { return 
 // ---- square root ------------------------------------------------------------
 __device__ __forceinline__ float gsqrt(float x) { return __fsqrt_rn(x); }
 __device__ __forceinline__ double gsqrt(double x) { return sqrt(x); }
-// Newton step on the FP32 root: s + (x - s^2) / (2 s)
+// Newton step on the FP32 root: s + (x - s^2) * (1 / (2 s)), the correction scaled by
+// the FP32 reciprocal (its error multiplies a term already 2^-24 small)
 __device__ __forceinline__ ff gsqrt(ff x)
 {
     if (!(x.hi > 0.f)) return ff_make(x.hi == 0.f ? 0.f : __int_as_float(0x7fc00000), 0.f);
-    float s = __fsqrt_rn(x.hi);
-    ff r = x - two_prod(s, s);
-    float c = __fdiv_rn(r.hi, 2.f * s);
-    return fast_two_sum(s, c);
+    const float s = __fsqrt_rn(x.hi);
+    const ff r = x - two_prod(s, s);
+    return fast_two_sum(s, r.hi * (0.5f * __frcp_rn(s)));
+}
+
+// ---- reciprocal ---------------------------------------------------------------------
+__device__ __forceinline__ float grcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double grcp(double x) { return 1.0 / x; }
+// 1 / x: FP32 reciprocal q of the leading part, one Newton step q (1 + e), e = 1 - x q
+// formed exactly in its leading part (1 - p.hi is exact for p.hi near 1)
+__device__ __forceinline__ ff grcp(ff x)
+{
+    const float q = __frcp_rn(x.hi);
+    const ff p = two_prod(x.hi, q);
+    float e = __fsub_rn(__fsub_rn(1.f, p.hi), p.lo);
+    e = __fmaf_rn(-x.lo, q, e);
+    return fast_two_sum(q, q * e);
 }
 
 // ---- exponential of a non-positive argument -----------------------------------

@@ -79,6 +79,326 @@ __device__ inline int value_axis_from_cov(const float c6[6])
     return ax;
 }
 
+// ---- blocked factor and inverse for voxels whose triangle lives in shared memory ----
+__device__ __forceinline__ float shfl_idx(float x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+__device__ __forceinline__ double shfl_idx(double x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+__device__ __forceinline__ ff shfl_idx(ff x, int src)
+{
+    return ff_make(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
+}
+
+// Right-looking Cholesky by panels of 16 columns, in place in the packed triangle:
+// (a) the 16 x 16 diagonal block is factored by warp 0 in registers (lane r holds row r,
+//     updates exchanged by shuffles); (b) the rows below the block solve against it, one
+//     row per thread; (c) the trailing triangle takes the rank-16 update in 4 x 4
+//     register tiles.  Three barriers per panel.  ild[k] receives 1 / L_kk.  Returns
+//     false at a non-positive pivot; s_dm holds the running min / max pivot.
+template <class T>
+__device__ bool chol_smem(T* L, int n, T* ild, float* s_dm, int* s_fail)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    for (int p0 = 0; p0 < n; p0 += 16) {
+        const int pw = min(16, n - p0);
+        if (wid == 0) {
+            T row[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                row[c] = (lane < pw && c <= lane) ? L[tri_off(p0 + c, n) + (lane - c)] : zero<T>();
+            bool bad = false;
+            float dmn = s_dm[0], dmx = s_dm[1];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                if (c < pw && !bad) {  // warp-uniform
+                    const T dcc = shfl_idx(row[c], c);
+                    const float dh = hi_of(dcc);
+                    if (!(dh > 0.f)) {
+                        bad = true;
+                    } else {
+                        dmn = fminf(dmn, dh);
+                        dmx = fmaxf(dmx, dh);
+                        const T lcc = gsqrt(dcc);
+                        const T il = grcp(lcc);
+                        if (lane == c) {
+                            row[c] = lcc;
+                            ild[p0 + c] = il;
+                        } else if (lane > c) {
+                            row[c] = row[c] * il;
+                        }
+                        const T lrc = row[c];
+#pragma unroll
+                        for (int r2 = c + 1; r2 < 16; ++r2) {
+                            const T v = shfl_idx(lrc, r2);  // l(r2, c)
+                            if (lane >= r2) row[r2] = gfnma(lrc, v, row[r2]);
+                        }
+                    }
+                }
+            }
+            if (!bad && lane < pw)
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    if (c <= lane) L[tri_off(p0 + c, n) + (lane - c)] = row[c];
+            if (lane == 0) {
+                s_dm[0] = dmn;
+                s_dm[1] = dmx;
+                if (bad) *s_fail = 1;
+            }
+        }
+        __syncthreads();
+        if (*s_fail) return false;
+        const int p1 = p0 + pw;
+        for (int i = p1 + tid; i < n; i += nthr) {  // (b) panel rows below the block
+            T a[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                a[c] = c < pw ? L[tri_off(p0 + c, n) + (i - p0 - c)] : zero<T>();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                if (c < pw) {
+                    a[c] = a[c] * ild[p0 + c];
+#pragma unroll
+                    for (int c2 = c + 1; c2 < 16; ++c2)
+                        if (c2 < pw) a[c2] = gfnma(a[c], L[tri_off(p0 + c, n) + (c2 - c)], a[c2]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < pw) L[tri_off(p0 + c, n) + (i - p0 - c)] = a[c];
+        }
+        __syncthreads();
+        const int m = n - p1;  // (c) trailing triangle, 4 x 4 tiles
+        if (m > 0) {
+            const int mb = (m + 3) >> 2;
+            const int ntiles = mb * (mb + 1) / 2;
+            for (int t = tid; t < ntiles; t += nthr) {
+                int bi = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+                while (bi > 0 && bi * (bi + 1) / 2 > t) --bi;
+                while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+                const int bj = t - bi * (bi + 1) / 2;
+                const int i0 = p1 + 4 * bi, j0 = p1 + 4 * bj;
+                T acc[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) acc[u][w] = zero<T>();
+                for (int c = 0; c < pw; ++c) {
+                    const T* col = L + tri_off(p0 + c, n) - (p0 + c);  // col[r] = L(r, p0 + c)
+                    T li[4], lj[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        li[u] = col[min(i0 + u, n - 1)];
+                        lj[u] = col[min(j0 + u, n - 1)];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) acc_fma(acc[u][w], li[u], lj[w]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int i = i0 + u, j = j0 + w;
+                        if (i < n && j <= i) {
+                            T* p = L + tri_off(j, n) + (i - j);
+                            *p = *p - acc_norm(acc[u][w]);
+                        }
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// X = L^-1 in place by row blocks of 16 (rows above the block hold X, rows from the
+// block down hold L): (1) Y(r, c) = sum_{k=c}^{r0-1} L(r0+r, k) X(k, c) for c < r0, four
+// rows per task so the X(k, c) loads are shared; (2) Y is parked in the block's rows;
+// (3) one thread per column solves with the 16 x 16 diagonal block (X_II = L_II^-1 from
+// the identity); (4) results written back.  Four barriers per 16 rows.  Needs
+// n <= blockDim.x; ild[k] = 1 / L_kk from the factorisation.
+template <class T>
+__device__ void inv_smem(T* L, int n, const T* ild)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int r0 = 0; r0 < n; r0 += 16) {
+        const int rb = min(16, n - r0);
+        const int ntask = 4 * r0;
+        T y[4][4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) y[s][u] = zero<T>();
+            const int t = tid + s * nthr;
+            if (t < ntask) {
+                const int c = t % r0, g = t / r0;
+                const T* xc = L + tri_off(c, n) - c;  // xc[k] = X(k, c)
+                for (int k = c; k < r0; ++k) {
+                    const T x = xc[k];
+                    const T* lk = L + tri_off(k, n) - k + r0;  // lk[r] = L(r0 + r, k)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = g + 4 * u;
+                        if (r < rb) acc_fma(y[s][u], lk[r], x);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int t = tid + s * nthr;
+            if (t < ntask) {
+                const int c = t % r0, g = t / r0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = g + 4 * u;
+                    if (r < rb) L[tri_off(c, n) + (r0 + r - c)] = acc_norm(y[s][u]);
+                }
+            }
+        }
+        __syncthreads();
+        const int c = tid;
+        const bool act = c < r0 + rb;
+        T z[16];
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                if (r < rb) {
+                    if (c < r0) z[r] = -L[tri_off(c, n) + (r0 + r - c)];
+                    else z[r] = from_f<T>(r0 + r == c ? 1.f : 0.f);
+                } else {
+                    z[r] = zero<T>();
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (q < rb) {
+                    z[q] = z[q] * ild[r0 + q];
+                    const T* lq = L + tri_off(r0 + q, n) - (r0 + q) + r0;  // lq[r] = L(r0 + r, r0 + q)
+#pragma unroll
+                    for (int r = q + 1; r < 16; ++r)
+                        if (r < rb) z[r] = gfnma(lq[r], z[q], z[r]);
+                }
+            }
+        }
+        __syncthreads();
+        if (act)
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (r < rb && r0 + r >= c) L[tri_off(c, n) + (r0 + r - c)] = z[r];
+        __syncthreads();
+    }
+}
+
+// Per-column variants for small voxels in the 8-byte types, where one barrier per column
+// beats the serial 16 x 16 diagonal blocks of the blocked variants.
+// Cholesky, right-looking with the unscaled trailing update: step k does
+// A_ij -= A_ik A_jk / A_kk for k < j <= i and scales column k-1 in the same phase (it is
+// not read by step k); one barrier per step.
+template <class T>
+__device__ void chol_percol_smem(T* L, int n, float& dmin, float& dmax, int& s_fail)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    T dprev = zero<T>();
+    T rs_prev = zero<T>();
+    for (int k = 0; k < n; ++k) {
+        __syncthreads();
+        const T d = L[tri_off(k, n)];
+        const float dh = hi_of(d);
+        if (!(dh > 0.f)) {
+            if (tid == 0) s_fail = 1;
+            break;
+        }
+        dmin = fminf(dmin, dh);
+        dmax = fmaxf(dmax, dh);
+        if (k > 0) {  // finish column k-1
+            T* ck = L + tri_off(k - 1, n);
+            for (int r = tid; r < n - (k - 1); r += nthr)
+                ck[r] = (r == 0) ? gsqrt(dprev) : ck[r] * rs_prev;
+        }
+        const T inv_d = from_f<T>(1.f) / d;
+        const T* colk = L + tri_off(k, n);
+        for (int j = k + 1 + wid; j < n; j += nw) {
+            const T s = colk[j - k] * inv_d;
+            T* colj = L + tri_off(j, n);
+            if (n - j <= 64) {  // short column: one update per lane
+                for (int i = j + lane; i < n; i += 32) colj[i - j] = gfnma(colk[i - k], s, colj[i - j]);
+                continue;
+            }
+            for (int i0 = j + lane; i0 < n; i0 += 128) {  // 4 independent updates
+                T a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = min(i0 + 32 * u, n - 1);
+                    a[u] = colk[i - k];
+                    b[u] = colj[i - j];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + 32 * u < n) colj[i0 + 32 * u - j] = gfnma(a[u], s, b[u]);
+            }
+        }
+        dprev = d;
+        rs_prev = from_f<T>(1.f) / gsqrt(d);
+    }
+    __syncthreads();
+    if (!s_fail && tid == 0) L[tri_off(n - 1, n)] = gsqrt(dprev);
+    __syncthreads();
+}
+
+// X = L^-1 in place, right-looking elimination of L X = I: step k finalises row k
+// (X_kc = B_kc / L_kk, c < k), then rows i > k take B_ic -= L_ik X_kc (c < k) and
+// B_ik = -L_ik / L_kk.  One warp owns row i, so it reads L_ik before the lane of column k
+// overwrites it; the diagonal keeps L_kk until a last pass writes 1 / L_kk.
+template <class T>
+__device__ void inv_percol_smem(T* L, int n)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    for (int k = 0; k < n; ++k) {
+        __syncthreads();
+        const T inv = from_f<T>(1.f) / L[tri_off(k, n)];
+        for (int c = tid; c < k; c += nthr) {
+            T* p = L + tri_off(c, n) + (k - c);
+            *p = (*p) * inv;
+        }
+        __syncthreads();
+        for (int i = k + 1 + wid; i < n; i += nw) {
+            const T m = L[tri_off(k, n) + (i - k)];
+            __syncwarp();
+            if (k < 64) {  // short row: one update per lane
+                for (int c = lane; c <= k; c += 32) {
+                    T* p = L + tri_off(c, n) + (i - c);
+                    *p = (c == k) ? -(m * inv) : gfnma(m, L[tri_off(c, n) + (k - c)], *p);
+                }
+                continue;
+            }
+            for (int c0 = lane; c0 <= k; c0 += 128) {  // 4 independent updates
+                T x[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = min(c0 + 32 * u, k);
+                    x[u] = L[tri_off(c, n) + (k - c)];
+                    b[u] = L[tri_off(c, n) + (i - c)];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = c0 + 32 * u;
+                    if (c <= k)
+                        L[tri_off(c, n) + (i - c)] = (c == k) ? -(m * inv) : gfnma(m, x[u], b[u]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < n; k += nthr) {
+        T* p = L + tri_off(k, n);
+        *p = from_f<T>(1.f) / (*p);
+    }
+    __syncthreads();
+}
+
 // ---- blocked factor and inverse for voxels whose triangle lives in global memory ----
 // The triangle (column-major packed, element (r, c) at tri_off(c, n) + r - c) stays in
 // the CTA's workspace slice; panels of it are staged in shared memory so that every
@@ -331,52 +651,17 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         if (!ok && tid == 0) s_fail = 1;
         __syncthreads();
     } else {
-        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
-        T dprev = zero<T>();
-        T rs_prev = zero<T>();
-        for (int k = 0; k < n; ++k) {
+        if (sizeof(T) == 8 && n <= 96) {
+            chol_percol_smem<T>(L, n, dmin, dmax, s_fail);
+        } else {
+            __shared__ float s_dm[2];
+            if (tid == 0) { s_dm[0] = 3.0e38f; s_dm[1] = 0.f; }
             __syncthreads();
-            const T d = L[tri_off(k, n)];
-            const float dh = hi_of(d);
-            if (!(dh > 0.f)) {
-                if (tid == 0) s_fail = 1;
-                break;
-            }
-            dmin = fminf(dmin, dh);
-            dmax = fmaxf(dmax, dh);
-            if (k > 0) {  // finish column k-1
-                T* ck = L + tri_off(k - 1, n);
-                for (int r = tid; r < n - (k - 1); r += nthr)
-                    ck[r] = (r == 0) ? gsqrt(dprev) : ck[r] * rs_prev;
-            }
-            const T inv_d = from_f<T>(1.f) / d;
-            const T* colk = L + tri_off(k, n);
-            for (int j = k + 1 + wid; j < n; j += nw) {
-                const T s = colk[j - k] * inv_d;
-                T* colj = L + tri_off(j, n);
-                if (n - j <= 64) {  // short column: one update per lane
-                    for (int i = j + lane; i < n; i += 32) colj[i - j] = gfnma(colk[i - k], s, colj[i - j]);
-                    continue;
-                }
-                for (int i0 = j + lane; i0 < n; i0 += 128) {  // 4 independent updates
-                    T a[4], b[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int i = min(i0 + 32 * u, n - 1);
-                        a[u] = colk[i - k];
-                        b[u] = colj[i - j];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (i0 + 32 * u < n) colj[i0 + 32 * u - j] = gfnma(a[u], s, b[u]);
-                }
-            }
-            dprev = d;
-            rs_prev = from_f<T>(1.f) / gsqrt(d);
+            chol_smem<T>(L, n, tmp, s_dm, &s_fail);
+            dmin = s_dm[0];
+            dmax = s_dm[1];
+            __syncthreads();
         }
-        __syncthreads();
-        if (!s_fail && tid == 0) L[tri_off(n - 1, n)] = gsqrt(dprev);
-        __syncthreads();
     }
     const bool ill = s_fail || (dmax > A.esc_cond * dmin);
     if (ill && A.escalate) {
@@ -412,57 +697,12 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     }
 
     if (!TRI_SMEM) big_invert<T>(L, n, W, P.rb);
-    // ---- A4': X = L^-1 in place, right-looking elimination of L X = I -------------
-    // step k: (a) row k is final: X_kc = B_kc / L_kk (c < k);
-    //         (b) rows i > k: B_ic -= L_ik X_kc (c < k) and B_ik = -L_ik / L_kk.
-    // B_ic overwrites L_ic (c < k, consumed at step c).  One warp owns row i in (b), so
-    // it reads L_ik before the lane of column k overwrites it.  The diagonal keeps L_kk
-    // until a last pass writes 1 / L_kk.  Two barriers per step; no thread runs a
-    // serial dot product.
+    // ---- A4': X = L^-1 in place (blocked by rows, see inv_smem) ---------------------
     if (TRI_SMEM) {
-        const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
-        for (int k = 0; k < n; ++k) {
-            __syncthreads();
-            const T inv = from_f<T>(1.f) / L[tri_off(k, n)];
-            for (int c = tid; c < k; c += nthr) {
-                T* p = L + tri_off(c, n) + (k - c);
-                *p = (*p) * inv;
-            }
-            __syncthreads();
-            for (int i = k + 1 + wid; i < n; i += nw) {
-                const T m = L[tri_off(k, n) + (i - k)];
-                __syncwarp();
-                if (k < 64) {  // short row: one update per lane
-                    for (int c = lane; c <= k; c += 32) {
-                        T* p = L + tri_off(c, n) + (i - c);
-                        *p = (c == k) ? -(m * inv) : gfnma(m, L[tri_off(c, n) + (k - c)], *p);
-                    }
-                    continue;
-                }
-                for (int c0 = lane; c0 <= k; c0 += 128) {  // 4 independent updates
-                    T x[4], b[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int c = min(c0 + 32 * u, k);
-                        x[u] = L[tri_off(c, n) + (k - c)];
-                        b[u] = L[tri_off(c, n) + (i - c)];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int c = c0 + 32 * u;
-                        if (c <= k)
-                            L[tri_off(c, n) + (i - c)] = (c == k) ? -(m * inv) : gfnma(m, x[u], b[u]);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        for (int k = tid; k < n; k += nthr) {
-            T* p = L + tri_off(k, n);
-            *p = from_f<T>(1.f) / (*p);
-        }
-        __syncthreads();
+        if (sizeof(T) == 8 && n <= 96) inv_percol_smem<T>(L, n);
+        else inv_smem<T>(L, n, tmp);
     }
+    __syncthreads();
 
     // ---- A5: alpha = X^T (X (f - m)) ----------------------------------------------
     for (int j = tid; j < n; j += nthr) {  // four partial sums in flight

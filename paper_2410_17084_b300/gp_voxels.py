@@ -25,7 +25,7 @@ EXPORTED = [
     "gp_voxels_init_gaussians", "gp_voxels_query_sizes", "gp_voxels_strerror",
     "gp_voxels_last_error", "gp_voxels_insert_scan", "gp_voxels_solve", "gp_voxels_scan_info",
     "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
-    "gp_voxels_last_launches",
+    "gp_voxels_last_launches", "gp_voxels_autotune",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.c_int32, P, P, P, P, P, P, P, P, P,
                                                   P, P, P]
         L.gp_voxels_last_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        L.gp_voxels_autotune.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P, P, P, P, P, P,
+                                         P, P, ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -215,6 +217,17 @@ def gp_voxels_release_scan(h, slot, stream=None) -> None:
     _check("gp_voxels_release_scan", lib().gp_voxels_release_scan(h, int(slot), _stream(stream)))
 
 
+def gp_voxels_autotune(h, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, mean, var, status,
+                       pos=None, scale=None, quat=None, stream=None) -> int:
+    changed = ctypes.c_int32()
+    rc = lib().gp_voxels_autotune(h, _ptr(xyz), _ptr(offsets), int(nvox), _ptr(centres),
+                                  _ptr(lam), _ptr(sf2), _ptr(sn2), _ptr(axis), _ptr(mean),
+                                  _ptr(var), _ptr(status), _ptr(pos), _ptr(scale), _ptr(quat),
+                                  _stream(stream), ctypes.byref(changed))
+    _check("gp_voxels_autotune", rc)
+    return changed.value
+
+
 def gp_voxels_last_launches(h) -> int:
     n = ctypes.c_int32()
     _check("gp_voxels_last_launches", lib().gp_voxels_last_launches(h, ctypes.byref(n)))
@@ -283,6 +296,14 @@ class GpVoxels:
                             out.get("scale"), out.get("quat"),
                             SOLVE_ONE_PER_LAUNCH if one_per_launch else 0, stream)
         return out
+
+    def autotune(self, xyz, offsets, centres, lam, sf2, sn2, init=True, stream=None) -> int:
+        """Choose the CTA size of every size bucket by timing this batch."""
+        nvox = offsets.shape[0] - 1
+        out = self.outputs(nvox, xyz.device, init)
+        return gp_voxels_autotune(self.h, xyz, offsets, nvox, centres, lam, sf2, sn2,
+                                  out["axis"], out["mean"], out["var"], out["status"],
+                                  out.get("pos"), out.get("scale"), out.get("quat"), stream)
 
     def init_gaussians(self, axis, centres, sf2, mean, var, status=None, stream=None) -> dict:
         nvox = axis.shape[0]

@@ -21,9 +21,19 @@ def main():
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--init", type=int, default=1)
     ap.add_argument("--workload", default="quadric",
-                    choices=["quadric", "mixed", "stress", "plane"])
+                    choices=["quadric", "mixed", "stress", "plane", "serving"])
+    ap.add_argument("--scans", type=int, default=12)
     a = ap.parse_args()
     build.build()
+    if a.workload == "serving":  # scans one after another through the serving path
+        from . import serve
+        scene = synth.lidar_scene()
+        scans = [synth.lidar_scan(scene, k) for k in range(a.scans)]
+        srv = serve.Server(serve.serving_config())
+        lat, wall, _ = srv.run(scans, realtime=False, max_inflight=1)
+        srv.close()
+        print("per-scan ms", [round(x * 1e3, 1) for x in lat.tolist()])
+        return
     gen = {"quadric": synth.quadric_batch, "mixed": synth.mixed_batch,
            "stress": synth.stress_batch, "plane": synth.plane_batch}[a.workload]
     b = gen(a.nvox)

@@ -286,3 +286,21 @@ def test_graph_replay_equals_direct_call(gpv):
         assert np.array_equal(v.cpu().numpy(), ref[k]), k
     assert ((ref["status"] & 2) != 0).any()  # the escalation pass ran inside the graph
     g.close()
+
+
+def test_autotune_keeps_parity(gpv, oracle):
+    """After the autotuner picks the CTA size of every bucket, results still match the
+    oracle within the tolerance."""
+    import torch
+    from paper_2410_17084_b300 import synth
+    full = synth.quadric_batch(4000, seed=51)
+    b = full.subset(np.concatenate([np.argsort(full.counts)[-30:], np.arange(600)]))
+    g = gpv.GpVoxels(_cfg(gpv, b, 1))
+    d = gpv.batch_to_device(b)
+    changed = g.autotune(d["xyz"], d["offsets"], d["centres"], d["lam"], d["sf2"], d["sn2"])
+    assert 0 <= changed <= 12
+    out = g.solve_csr(d["xyz"], d["offsets"], d["centres"], d["lam"], d["sf2"], d["sn2"])
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    g.close()
+    _check(gpv, b, res, oracle, MEAN_TOL, VAR_TOL, f"autotuned (changed {changed})")
