@@ -113,6 +113,9 @@ def ff_peak_tflops(sm_mhz: float) -> float:
     return 148 * 128 * sm_mhz * 1e6 / FF_OPS_PER_FMA * 2 / 1e12
 
 
+SOLVE_KERNEL_SOURCES = ("gpv_init.cuh", "gpv_internal.h", "gpv_num.cuh", "gpv_solve.cu")
+
+
 def traffic_from_profiles(nvox_step: int):
     """DRAM bytes per step of the solve kernels from the committed ncu summary, if it was
     taken on the current kernel sources (else None)."""
@@ -120,9 +123,8 @@ def traffic_from_profiles(nvox_step: int):
     import re
     csrc = os.path.join(ROOT, "paper_2410_17084_b300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in SOLVE_KERNEL_SOURCES:  # the sources the solve kernels are compiled from
+        h.update(open(os.path.join(csrc, f), "rb").read())
     sha = h.hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "solve_ff_quadric_traffic.md")
     if not os.path.exists(path):

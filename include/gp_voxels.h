@@ -60,7 +60,9 @@ enum {
     GPV_VOX_ESCALATED = 2,  /* re-solved in FP64 after the conditioning check */
     GPV_VOX_NOT_SPD = 4,    /* Gram not positive definite in the final precision */
     GPV_VOX_TRUNCATED = 8,  /* bucket overflowed; oldest points were dropped */
-    GPV_VOX_TOO_LARGE = 16  /* n > max_points: not processed; prior written */
+    GPV_VOX_TOO_LARGE = 16, /* n > max_points: not processed; prior written */
+    GPV_VOX_CONVERGED = 32  /* serving with the state machine on: the voxel had
+                               converged (type d, Sec. 3.3), not solved; prior written */
 };
 
 /* Arithmetic of the solve. */
@@ -100,7 +102,23 @@ typedef struct {
                             (0 = max_scan_voxels * max_points) */
     float lambda, sf2, sn2; /* kernel and noise of the serving solve (Sec. 3.1 uses
                             lambda = 1 and no signal variance, sf2 = 1) */
+    /* voxel state machine of Sec. 3.3 (serving only; eta <= 0 turns it off) */
+    float eta;           /* convergence threshold: a solved voxel whose mean predicted
+                            variance over its G x G nodes is <= eta * sf2 is converged
+                            (type d) and no longer solved; paper: 0.3 (hyperparameter
+                            table) */
+    float noise_floor;   /* lower bound of a point's fed-back noise variance (keeps the
+                            Gram matrix conditioned); the paper gives none */
 } gp_voxels_config;
+
+/* Voxel types of Sec. 3.3 (gp_voxels_scan_types, gp_voxels_type_counts). */
+enum {
+    GPV_TYPE_A = 0, /* fewer than tau points: not processed */
+    GPV_TYPE_B = 1, /* at least tau points, not yet solved into the map */
+    GPV_TYPE_C = 2, /* solved, mean variance above eta * sf2: active, re-solved when
+                       new points arrive, with the fed-back noise of its old points */
+    GPV_TYPE_D = 3  /* converged: not processed any more */
+};
 
 /* Fill *cfg with the paper's defaults (size 0.2, n_s = n_r = 3, tau = 10, lambda 1
  * is a per-call input) and the library's limits.  Never fails for non-NULL cfg. */
@@ -140,6 +158,25 @@ GPV_API int gp_voxels_solve_csr(gp_voxels_t* h, const float* d_xyz, const int64_
                         const float* d_sf2, const float* d_sn2, uint8_t* d_axis,
                         float* d_mean, float* d_var, uint32_t* d_status, float* d_pos,
                         float* d_scale, float* d_quat, uint32_t flags, gpv_stream_t stream);
+
+/* Voxel-GPR with a noise variance per point (Sec. 3.3: the points of an active voxel
+ * carry the variance estimated by its previous solve, new points the sensor's).  As
+ * gp_voxels_solve_csr, with the Gram diagonal sf2 + d_noise[p] instead of sf2 + sn2:
+ *   d_noise [N]   FP32 noise variance of every point (NULL: d_sn2 of its voxel)
+ *   d_pvar  [N]   optional output: posterior variance of the latent surface at every
+ *                 input, sf2 - k_p^T (K + D)^-1 k_p with k_p the kernel column of point
+ *                 p (no noise); computed as d_p (1 - d_p [(K + D)^-1]_pp).  Left
+ *                 unwritten for voxels not solved (status BELOW_TAU, TOO_LARGE, NOT_SPD).
+ * In GPV_PREC_FP32 the subtraction in d_pvar loses about log10(n) digits of FP32;
+ * use GPV_PREC_MIXED or FP64 where d_pvar feeds the next solve.
+ * Errors: GPV_EINVAL, GPV_ECUDA. */
+GPV_API int gp_voxels_solve_csr_noise(gp_voxels_t* h, const float* d_xyz,
+                              const int64_t* d_offsets, int32_t nvox, const float* d_centres,
+                              const float* d_lambda, const float* d_sf2, const float* d_sn2,
+                              const float* d_noise, uint8_t* d_axis, float* d_mean,
+                              float* d_var, uint32_t* d_status, float* d_pos, float* d_scale,
+                              float* d_quat, float* d_pvar, uint32_t flags,
+                              gpv_stream_t stream);
 
 /* Gaussian initialisation from given predictions (Sec. 3.2, Eq. 6-8): for each of the
  * n_s x n_s subgrids of each voxel, weights w = 1 / max(var, 1e-6 sf2), position
@@ -190,6 +227,32 @@ GPV_API int gp_voxels_solve(gp_voxels_t* h, int32_t slot, uint8_t* d_axis, float
                             float* d_var, uint32_t* d_status, float* d_pos, float* d_scale,
                             float* d_quat, int64_t* d_keys, float* d_centres,
                             gpv_stream_t stream);
+
+/* With the state machine on (eta > 0), the serving path follows Sec. 3.3:
+ *  - every stored point carries a noise variance: the config's sn2 when inserted,
+ *    then the posterior variance at that point from the last solve of its voxel
+ *    (at least noise_floor);
+ *  - gp_voxels_insert_scan records the type of every visited voxel: (a) fewer than tau
+ *    points, (b) enough points but never solved, (c) active, (d) converged;
+ *  - gp_voxels_solve solves the rows of types (b) and (c) with those per-point noises,
+ *    writes the posterior variance back to the points, and moves each solved voxel to
+ *    (d) when its mean predicted variance is <= eta * sf2, else to (c).  Rows of type
+ *    (d) get GPV_VOX_CONVERGED and the prior.
+ * Types depend on the previous scans' solves, so in this mode each scan must be solved
+ * before the next one is inserted: gp_voxels_insert_scan returns GPV_EINVAL while an
+ * inserted scan awaits its gp_voxels_solve, and it waits on the device for that
+ * solve's state update. */
+
+/* Voxel type (GPV_TYPE_*) of every row of a solved slot, before (d_before) and after
+ * (d_after) the solve, uint8 [max_scan_voxels] each, either may be NULL.  After the
+ * solve a voxel that could not be solved (NOT_SPD, TOO_LARGE) keeps type (b) or (c).
+ * Errors: GPV_EINVAL (no store, state machine off, bad slot), GPV_ECUDA. */
+GPV_API int gp_voxels_scan_types(gp_voxels_t* h, int32_t slot, uint8_t* d_before,
+                                 uint8_t* d_after, gpv_stream_t stream);
+
+/* Number of stored voxels of each type (a)-(d) after the work queued so far
+ * (synchronises the device): h_counts[4].  Errors: GPV_EINVAL, GPV_ECUDA. */
+GPV_API int gp_voxels_type_counts(gp_voxels_t* h, int64_t* h_counts);
 
 /* Counts of a slot's scan: rows (visited voxels, at most max_scan_voxels), snapshot
  * points, flags (bit 0: hash full, points dropped; bit 1: more than max_scan_voxels

@@ -308,6 +308,91 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
+/* Voxel-GPR with a noise variance per training point (Sec. 3.3: the   */
+/* points of an active voxel carry the variance estimated by its last  */
+/* solve, new points the sensor variance): A = K + diag(noise).        */
+/* Besides mean/var at the query nodes (as gpo_solve_voxel) it returns  */
+/* pvar[i], the posterior variance at training input x_i from its      */
+/* definition sf2 - k_i^T A^-1 k_i with k_i = (k(x_i, x_j))_j (no noise),  */
+/* computed as sf2 - |L^-1 k_i|^2.                                     */
+/* ------------------------------------------------------------------ */
+int gpo_solve_voxel_hetero(const float* xyz, int64_t n, const float* centre, double size, int G,
+                           double lambda, double sf2, const double* noise, int mean_mode,
+                           int axis_override, int* axis_out, double* mean, double* var,
+                           double* pvar)
+{
+    int axis = axis_override >= 0 ? axis_override : gpo_pca_axis(xyz, n, NULL, NULL);
+    int p1, p2;
+    param_axes(axis, &p1, &p2);
+    *axis_out = axis;
+
+    double* x1 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* x2 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* fm = (double*)malloc(sizeof(double) * (size_t)n);
+    double* A = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    double* alpha = (double*)malloc(sizeof(double) * (size_t)n);
+    double* k = (double*)malloc(sizeof(double) * (size_t)n);
+    double* z = (double*)malloc(sizeof(double) * (size_t)n);
+
+    for (int64_t i = 0; i < n; ++i) {
+        x1[i] = (double)xyz[3 * i + p1] - (double)centre[p1];
+        x2[i] = (double)xyz[3 * i + p2] - (double)centre[p2];
+        fm[i] = (double)xyz[3 * i + axis] - (double)centre[axis];
+    }
+    double m = 0.0;
+    if (mean_mode == 1) {
+        for (int64_t i = 0; i < n; ++i) m += fm[i];
+        m /= (double)n;
+    }
+    for (int64_t i = 0; i < n; ++i) fm[i] -= m;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double d1 = x1[i] - x1[j], d2 = x2[i] - x2[j];
+            A[i * n + j] = sf2 * exp(-lambda * (d1 * d1 + d2 * d2)) + (i == j ? noise[i] : 0.0);
+        }
+    int status = GPO_OK;
+    if (cholesky(A, n) != 0) {
+        status = GPO_NOT_SPD;
+        goto done;
+    }
+    forward_sub(A, n, fm, y);
+    backward_sub(A, n, y, alpha);
+    for (int i = 0; i < G; ++i) {
+        double u = grid_node(i, G, size);
+        for (int j = 0; j < G; ++j) {
+            double v = grid_node(j, G, size);
+            double mu = m;
+            for (int64_t t = 0; t < n; ++t) {
+                double d1 = x1[t] - u, d2 = x2[t] - v;
+                k[t] = sf2 * exp(-lambda * (d1 * d1 + d2 * d2));
+                mu += k[t] * alpha[t];
+            }
+            forward_sub(A, n, k, z);
+            double zz = 0.0;
+            for (int64_t t = 0; t < n; ++t) zz += z[t] * z[t];
+            double vv = sf2 - zz;
+            mean[i * G + j] = mu;
+            var[i * G + j] = vv > 0.0 ? vv : 0.0;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {  /* posterior variance at the training inputs */
+        for (int64_t t = 0; t < n; ++t) {
+            double d1 = x1[t] - x1[i], d2 = x2[t] - x2[i];
+            k[t] = sf2 * exp(-lambda * (d1 * d1 + d2 * d2));
+        }
+        forward_sub(A, n, k, z);
+        double zz = 0.0;
+        for (int64_t t = 0; t < n; ++t) zz += z[t] * z[t];
+        double vv = sf2 - zz;
+        pvar[i] = vv > 0.0 ? vv : 0.0;
+    }
+done:
+    free(x1); free(x2); free(fm); free(A); free(y); free(alpha); free(k); free(z);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* Quaternion (w, x, y, z) of a proper rotation matrix R (row-major), */
 /* the textbook trace/major-diagonal branches; sign fixed to w >= 0.  */
 /* ------------------------------------------------------------------ */

@@ -7,7 +7,7 @@ The CUDA product path (``paper_2410_17084_b300``) never imports it.
 
 Functions follow GS-LIVM (arXiv 2410.17084): Voxel-GPR of Sec. 3.1 (Alg. 1, Eq. 2-3),
 the Gaussian initialisation of Sec. 3.2 (Eq. 6-8) and ALG.STORE / ALG.HASH of the
-supplementary Alg. 2.
+supplementary Alg. 2, and the voxel state machine with variance feedback of Sec. 3.3.
 """
 from __future__ import annotations
 
@@ -23,6 +23,7 @@ _LIB = os.path.join(_HERE, "libgp_oracle.so")
 
 BELOW_TAU = 1
 NOT_SPD = 4
+CONVERGED = 32  # map update of Sec. 3.3: a converged voxel is not solved
 
 
 def build(force: bool = False) -> str:
@@ -51,6 +52,9 @@ def lib():
         _lib.gpo_solve_voxel.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, P, P, P]
+        _lib.gpo_solve_voxel_hetero.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, P, ctypes.c_int,
+                                                ctypes.c_int, P, P, P, P]
         _lib.gpo_init_voxel.argtypes = [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, P, P, P, P]
@@ -111,6 +115,23 @@ def solve_voxel(xyz, centre, size, G, lam, sf2, sn2, mean_mode=1, axis_override=
                                float(lam), float(sf2), float(sn2), int(mean_mode),
                                int(axis_override), ctypes.byref(ax), _p(mean), _p(var))
     return st, ax.value, mean, var
+
+
+def solve_voxel_hetero(xyz, centre, size, G, lam, sf2, noise, mean_mode=1, axis_override=-1):
+    """Voxel-GPR with a noise variance per training point (Sec. 3.3): (status, axis,
+    mean[G*G], var[G*G], pvar[n]) with pvar the posterior variance at the inputs."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    centre = np.ascontiguousarray(centre, dtype=np.float32).reshape(3)
+    noise = np.ascontiguousarray(noise, dtype=np.float64).reshape(-1)
+    mean = np.zeros(G * G)
+    var = np.zeros(G * G)
+    pvar = np.zeros(xyz.shape[0])
+    ax = ctypes.c_int(0)
+    st = lib().gpo_solve_voxel_hetero(_p(xyz), xyz.shape[0], _p(centre), float(size), int(G),
+                                      float(lam), float(sf2), _p(noise), int(mean_mode),
+                                      int(axis_override), ctypes.byref(ax), _p(mean), _p(var),
+                                      _p(pvar))
+    return st, ax.value, mean, var, pvar
 
 
 def init_voxel(mean, var, axis, centre, size, G, n_s, n_r, sf2, init_mode=0):
@@ -180,11 +201,17 @@ class VoxelStore:
     oldest meaning smallest (scan_id, index-in-scan).  Points are held in that order.
     """
 
-    def __init__(self, size: float, max_points: int):
+    # voxel types of Sec. 3.3
+    BELOW, READY, ACTIVE, CONVERGED = 0, 1, 2, 3
+
+    def __init__(self, size: float, max_points: int, sensor_var: float = 0.0):
         self.size = np.float32(size)
         self.max_points = int(max_points)
+        self.sensor_var = float(np.float32(sensor_var))
         self.buckets: dict[tuple, list] = {}
+        self.noise: dict[tuple, list] = {}   # noise variance of every stored point
         self.total: dict[tuple, int] = {}
+        self.state: dict[tuple, int] = {}
 
     def insert_scan(self, xyz: np.ndarray) -> list:
         xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
@@ -194,14 +221,69 @@ class VoxelStore:
         for i in range(xyz.shape[0]):  # Alg. 2, one point at a time
             k = (int(keys[i, 0]), int(keys[i, 1]), int(keys[i, 2]))
             b = self.buckets.setdefault(k, [])
+            nz = self.noise.setdefault(k, [])
             b.append(xyz[i].copy())
+            nz.append(self.sensor_var)
             if len(b) > self.max_points:
                 b.pop(0)
+                nz.pop(0)
             self.total[k] = self.total.get(k, 0) + 1
             if k not in seen:
                 seen.add(k)
                 touched.append(k)
         return touched
+
+    def voxel_type(self, key, tau: int) -> int:
+        """Type of a stored voxel (Sec. 3.3): (d) converged and (c) active come from its
+        solves; otherwise (b) once it holds tau points, else (a)."""
+        st = self.state.get(key, self.BELOW)
+        if st in (self.ACTIVE, self.CONVERGED):
+            return st
+        return self.READY if len(self.buckets.get(key, ())) >= tau else self.BELOW
+
+    def process_scan(self, xyz, G: int, lam: float, sf2: float, tau: int, eta: float,
+                     noise_floor: float, mean_mode: int = 1, axis_of=None, decide=None):
+        """One scan through the map update of Sec. 3.3.
+
+        The scan is stored (Alg. 2); each visited voxel is classified as (a)-(d) before
+        any solve.  Types (b) and (c) are solved with the noise variance every stored
+        point carries (the sensor's for new points, the last posterior variance at the
+        point for old ones); the stored points then take the new posterior variance at
+        them (at least noise_floor; kept as FP32 like the store), and the voxel becomes
+        (d) when the mean predicted variance over its G x G nodes is at most
+        eta * sf2, else (c).  Types (a) and (d) are not processed.
+
+        axis_of(key, pts) may return a value axis to impose (for axis-ambiguous voxels)
+        or -1; decide(key, mean_var, threshold) may return the converged flag where the
+        comparison is within rounding of the threshold, or None.
+        Returns one dict per visited voxel, in S_updated order."""
+        touched = self.insert_scan(xyz)
+        types = [self.voxel_type(k, tau) for k in touched]
+        thr = float(np.float32(np.float32(eta) * np.float32(sf2)))
+        out = []
+        for k, ty in zip(touched, types):
+            pts = self.points(k)
+            r = {"key": k, "type_before": ty, "n": pts.shape[0]}
+            if ty in (self.READY, self.ACTIVE):
+                ax = axis_of(k, pts) if axis_of else -1
+                nz = np.array(self.noise[k], dtype=np.float64)
+                st, axis, mean, var, pvar = solve_voxel_hetero(
+                    pts, self.centre(k), float(self.size), G, lam, sf2, nz, mean_mode, ax)
+                r.update(status=st, axis=axis, mean=mean, var=var, pvar=pvar, noise=nz)
+                if st == 0:
+                    fl = np.float32(noise_floor)
+                    self.noise[k] = [float(max(np.float32(v), fl)) for v in pvar]
+                    mv = float(np.mean(var))
+                    conv = decide(k, mv, thr) if decide else None
+                    if conv is None:
+                        conv = mv <= thr
+                    self.state[k] = self.CONVERGED if conv else self.ACTIVE
+                    r["mean_var"] = mv
+                r["type_after"] = self.state.get(k, ty) if st == 0 else ty
+            else:
+                r.update(status=CONVERGED if ty == self.CONVERGED else 1, type_after=ty)
+            out.append(r)
+        return out
 
     def points(self, key) -> np.ndarray:
         return np.array(self.buckets[key], dtype=np.float32).reshape(-1, 3)

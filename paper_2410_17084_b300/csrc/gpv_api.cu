@@ -110,6 +110,7 @@ static int validate(const gp_voxels_config* c)
             return GPV_EINVAL;
         if (c->snap_points < 0) return GPV_EINVAL;
         if (!(c->lambda > 0.f) || !(c->sf2 > 0.f) || !(c->sn2 >= 0.f)) return GPV_EINVAL;
+        if (c->eta > 0.f && !(c->noise_floor >= 0.f && c->eta < 3.0e38f)) return GPV_EINVAL;
     }
     return GPV_OK;
 }
@@ -363,7 +364,9 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
                            const int64_t* d_offsets, int32_t nvox, const int32_t* d_nvox,
                            const float* d_centres, const float* d_lambda, const float* d_sf2,
                            const float* d_sn2, uint8_t* d_axis, float* d_mean, float* d_var,
-                           uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat)
+                           uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat,
+                           const float* d_noise = nullptr, float* d_pvar = nullptr,
+                           const uint8_t* d_skip = nullptr)
 {
     const gp_voxels_config& c = h->cfg;
     const int kind = prec_kind(c.precision);
@@ -377,6 +380,7 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     a.escalate = kind == PREC_FF ? 1 : 0;
     a.axis = d_axis; a.mean = d_mean; a.var = d_var; a.status = d_status;
     a.pos = d_pos; a.scale = d_scale; a.quat = d_quat;
+    a.noise = d_noise; a.pvar = d_pvar; a.skip = d_skip;
     a.esc_list = x.d_esc_list; a.esc_count = x.d_esc_count;
     a.gws = x.d_gws; a.gws_stride = h->gws_stride;
     a.max_points = c.max_points;
@@ -389,13 +393,15 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
                            const float* d_centres, const float* d_lambda, const float* d_sf2,
                            const float* d_sn2, uint8_t* d_axis, float* d_mean, float* d_var,
                            uint32_t* d_status, float* d_pos, float* d_scale, float* d_quat,
-                           uint32_t flags, cudaStream_t s)
+                           uint32_t flags, cudaStream_t s, const float* d_noise = nullptr,
+                           float* d_pvar = nullptr, const uint8_t* d_skip = nullptr)
 {
     const gp_voxels_config& c = h->cfg;
     const int kind = prec_kind(c.precision);
     const PrecPlan& P = h->plan[kind];
     SolveArgs a = make_args(h, x, d_xyz, d_offsets, nvox, d_nvox, d_centres, d_lambda, d_sf2,
-                            d_sn2, d_axis, d_mean, d_var, d_status, d_pos, d_scale, d_quat);
+                            d_sn2, d_axis, d_mean, d_var, d_status, d_pos, d_scale, d_quat,
+                            d_noise, d_pvar, d_skip);
     CK(launch_classify(a, P.d_hi, P.nb, x.d_bcount, x.d_bbase, x.d_bcursor, x.d_work,
                        x.d_next, x.d_esc_count, s));
     h->last_launches = 3;  // classify, bucket offsets, scatter
@@ -482,6 +488,20 @@ extern "C" int gp_voxels_solve_csr(gp_voxels_t* h, const float* d_xyz, const int
                                    float* d_scale, float* d_quat, uint32_t flags,
                                    gpv_stream_t stream)
 {
+    return gp_voxels_solve_csr_noise(h, d_xyz, d_offsets, nvox, d_centres, d_lambda, d_sf2,
+                                     d_sn2, nullptr, d_axis, d_mean, d_var, d_status, d_pos,
+                                     d_scale, d_quat, nullptr, flags, stream);
+}
+
+extern "C" int gp_voxels_solve_csr_noise(gp_voxels_t* h, const float* d_xyz,
+                                         const int64_t* d_offsets, int32_t nvox,
+                                         const float* d_centres, const float* d_lambda,
+                                         const float* d_sf2, const float* d_sn2,
+                                         const float* d_noise, uint8_t* d_axis, float* d_mean,
+                                         float* d_var, uint32_t* d_status, float* d_pos,
+                                         float* d_scale, float* d_quat, float* d_pvar,
+                                         uint32_t flags, gpv_stream_t stream)
+{
     if (!h || nvox < 0 || nvox > h->cfg.max_voxels) return GPV_EINVAL;
     if (nvox == 0) return GPV_OK;  // nothing to read or write
     if (!d_offsets || !d_axis || !d_mean || !d_var || !d_status) return GPV_EINVAL;
@@ -491,7 +511,7 @@ extern "C" int gp_voxels_solve_csr(gp_voxels_t* h, const float* d_xyz, const int
     if (flags & ~(uint32_t)GPV_SOLVE_ONE_PER_LAUNCH) return GPV_EINVAL;
     return gpv_solve_queue(h, h->main, d_xyz, d_offsets, nvox, nullptr, d_centres, d_lambda,
                            d_sf2, d_sn2, d_axis, d_mean, d_var, d_status, d_pos, d_scale, d_quat,
-                           flags, (cudaStream_t)stream);
+                           flags, (cudaStream_t)stream, d_noise, d_pvar, nullptr);
 }
 
 extern "C" int gp_voxels_init_gaussians(gp_voxels_t* h, int32_t nvox, const uint8_t* d_axis,
@@ -523,14 +543,17 @@ extern "C" int gp_voxels_insert_scan(gp_voxels_t* h, const float* d_xyz, int64_t
     for (int i = 0; i < st->nslots; ++i)
         if (!st->slots[i].busy) { si = i; break; }
     if (si < 0) return GPV_EFULL;
+    if (st->feedback && st->unsolved >= 0) return GPV_EINVAL;  // solve the previous scan first
     cudaStream_t s = (cudaStream_t)stream;
     gpv_scan_slot& S = st->slots[si];
     CK(cudaStreamWaitEvent(s, S.free_ev, 0));      // the slot's previous scan is done
     CK(cudaStreamWaitEvent(s, st->ev_insert, 0));  // inserts follow call order
+    if (st->feedback) CK(cudaStreamWaitEvent(s, st->ev_fb, 0));  // types and noises are current
     CK(store_insert(st, si, d_xyz, (int)npts, s, &h->cfg));
     CK(cudaEventRecord(st->ev_insert, s));
     CK(cudaEventRecord(S.ins_ev, s));
     S.busy = true;
+    if (st->feedback) st->unsolved = si;
     *slot_out = si;
     return GPV_OK;
 }
@@ -550,13 +573,21 @@ extern "C" int gp_voxels_solve(gp_voxels_t* h, int32_t slot, uint8_t* d_axis, fl
     cudaStream_t s = (cudaStream_t)stream;
     // the slot's insert may have been queued on another stream
     CK(cudaStreamWaitEvent(s, S.ins_ev, 0));
+    const bool fb = st->feedback;
     int rc = gpv_solve_queue(h, h->sctx[slot], S.snap, S.snapoff, st->max_vox, S.counters,
                              S.centres, S.lam, S.sf2, S.sn2, d_axis, d_mean, d_var, d_status,
-                             d_pos, d_scale, d_quat, 0, s);
+                             d_pos, d_scale, d_quat, 0, s, fb ? S.snap_noise : nullptr,
+                             fb ? S.snap_pvar : nullptr, fb ? S.rskip : nullptr);
     if (rc != GPV_OK) return rc;
     CK(store_or_flags(st, slot, d_status, s));
     CK(store_copy_rows(st, slot, d_keys, d_centres, s));
     h->last_launches += 1 + ((d_keys || d_centres) ? 1 : 0);
+    if (fb) {  // Sec. 3.3: noise feedback and type transitions, before the next insert
+        CK(store_feedback(st, slot, d_status, d_var, &h->cfg, s));
+        CK(cudaEventRecord(st->ev_fb, s));
+        if (st->unsolved == slot) st->unsolved = -1;
+        h->last_launches += 1;
+    }
     return GPV_OK;
 }
 
@@ -586,6 +617,33 @@ extern "C" int gp_voxels_release_scan(gp_voxels_t* h, int32_t slot, gpv_stream_t
     gpv_scan_slot& S = h->store->slots[slot];
     CK(cudaEventRecord(S.free_ev, (cudaStream_t)stream));
     S.busy = false;
+    if (h->store->unsolved == slot) h->store->unsolved = -1;  // released unsolved: no update
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_scan_types(gp_voxels_t* h, int32_t slot, uint8_t* d_before,
+                                    uint8_t* d_after, gpv_stream_t stream)
+{
+    if (!h || !h->store || !h->store->feedback || slot < 0 || slot >= h->store->nslots ||
+        !h->store->slots[slot].busy)
+        return GPV_EINVAL;
+    if (!d_before && !d_after) return GPV_OK;
+    CK(store_copy_types(h->store, slot, d_before, d_after, (cudaStream_t)stream));
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_type_counts(gp_voxels_t* h, int64_t* h_counts)
+{
+    if (!h || !h->store || !h_counts) return GPV_EINVAL;
+    unsigned long long* d = nullptr;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMalloc(&d, 4 * sizeof(unsigned long long)));
+    cudaError_t e = store_type_counts(h->store, h->cfg.tau, d, 0);
+    unsigned long long c[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(c, d, sizeof(c), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int i = 0; i < 4; ++i) h_counts[i] = (int64_t)c[i];
     return GPV_OK;
 }
 

@@ -15,6 +15,7 @@ enum : uint32_t {
     VOX_NOT_SPD = 4u,
     VOX_TRUNCATED = 8u,
     VOX_TOO_LARGE = 16u,
+    VOX_CONVERGED = 32u,
 };
 
 constexpr int kThreads = 512;   // largest CTA size of the solve kernels
@@ -31,6 +32,8 @@ struct SolveArgs {
     const float* lam;
     const float* sf2;
     const float* sn2;
+    const float* noise;         // per-point noise variance (replaces sn2 on the diagonal), or null
+    const uint8_t* skip;        // per-voxel: nonzero = converged, not solved (or null)
     int32_t nvox;               // rows of the outputs (stride of the escalation lists)
     const int32_t* nvox_dev;    // device count of rows to solve (serving), or null
     float size;
@@ -46,6 +49,7 @@ struct SolveArgs {
     float* pos;
     float* scale;
     float* quat;
+    float* pvar;                // per-point posterior variance at the inputs, or null
     // work queue of this launch
     const int32_t* work;
     const int32_t* work_base;   // device: first entry of this launch in work[] (or null)

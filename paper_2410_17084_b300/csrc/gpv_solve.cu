@@ -633,8 +633,8 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             const T d1b = x1[re[1]] - x1[ce[1]], d2b = x2[re[1]] - x2[ce[1]];
             T ka = sf2 * gexp(nlam * (d1a * d1a + d2a * d2a));
             T kb = sf2 * gexp(nlam * (d1b * d1b + d2b * d2b));
-            if (re[0] == ce[0]) ka = ka + sn2;
-            if (re[1] == ce[1]) kb = kb + sn2;
+            if (re[0] == ce[0]) ka = ka + (A.noise ? from_f<T>(__ldg(A.noise + beg + re[0])) : sn2);
+            if (re[1] == ce[1]) kb = kb + (A.noise ? from_f<T>(__ldg(A.noise + beg + re[1])) : sn2);
             L[e0] = ka;
             if (e0 + nthr < ntri) L[e1] = kb;
         }
@@ -703,6 +703,26 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         else inv_smem<T>(L, n, tmp);
     }
     __syncthreads();
+
+    // ---- posterior variance at the inputs (per-point noise feedback, Sec. 3.3) -------
+    // With A = K + D, k_i = A e_i - d_i e_i gives sf2 - k_i^T A^-1 k_i
+    // = d_i (1 - d_i (A^-1)_ii), and (A^-1)_ii is the squared norm of column i of X,
+    // which is contiguous in the packed layout.
+    if (A.pvar) {
+        for (int i = tid; i < n; i += nthr) {
+            const T* col = L + tri_off(i, n);
+            T s2[2] = {zero<T>(), zero<T>()};
+            int t = 0;
+            for (; t + 1 < n - i; t += 2) {
+                acc_fma(s2[0], col[t], col[t]);
+                acc_fma(s2[1], col[t + 1], col[t + 1]);
+            }
+            if (t < n - i) acc_fma(s2[0], col[t], col[t]);
+            const T d = A.noise ? from_f<T>(__ldg(A.noise + beg + i)) : sn2;
+            const float pv = to_f(d * (from_f<T>(1.f) - d * (acc_norm(s2[0]) + acc_norm(s2[1]))));
+            A.pvar[beg + i] = fmaxf(pv, 0.f);
+        }
+    }
 
     // ---- A5: alpha = X^T (X (f - m)) ----------------------------------------------
     for (int j = tid; j < n; j += nthr) {  // four partial sums in flight
@@ -872,7 +892,8 @@ __global__ void k_classify(SolveArgs A, const int* bucket_hi, int nb, int32_t* b
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= (A.nvox_dev ? min(*A.nvox_dev, A.nvox) : A.nvox)) return;
     const int64_t n = A.offsets[v + 1] - A.offsets[v];
-    if (n < A.tau || n <= 0 || n > A.max_points) {
+    const bool skip = A.skip && A.skip[v];
+    if (skip || n < A.tau || n <= 0 || n > A.max_points) {
         const int GG = A.G * A.G;
         const float sf2 = A.sf2[v];
         for (int q = 0; q < GG; ++q) {
@@ -880,7 +901,7 @@ __global__ void k_classify(SolveArgs A, const int* bucket_hi, int nb, int32_t* b
             A.var[(int64_t)v * GG + q] = sf2;
         }
         A.axis[v] = 255;
-        A.status[v] = n > A.max_points ? VOX_TOO_LARGE : VOX_BELOW_TAU;
+        A.status[v] = skip ? VOX_CONVERGED : (n > A.max_points ? VOX_TOO_LARGE : VOX_BELOW_TAU);
         if (A.pos) {
             const int NG = A.n_s * A.n_s;
             for (int g = 0; g < NG; ++g) {
@@ -923,7 +944,7 @@ __global__ void k_scatter(SolveArgs A, const int* bucket_hi, int nb, const int32
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= (A.nvox_dev ? min(*A.nvox_dev, A.nvox) : A.nvox)) return;
     const int64_t n = A.offsets[v + 1] - A.offsets[v];
-    if (n < A.tau || n <= 0 || n > A.max_points) return;
+    if ((A.skip && A.skip[v]) || n < A.tau || n <= 0 || n > A.max_points) return;
     int b = nb - 1;
     for (int k = 0; k < nb; ++k)
         if (n <= bucket_hi[k]) { b = k; break; }

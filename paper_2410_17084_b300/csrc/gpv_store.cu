@@ -213,8 +213,9 @@ __global__ void k_fill(const int32_t* slot_of, const int32_t* tmap, const int32_
 // one warp per visited voxel: deterministic order, ring append, marks cleared
 __global__ void k_append(const float* xyz, const int32_t* counters, const int32_t* touched,
                          const int32_t* segsz, const int32_t* segoff, const int32_t* seg,
-                         int32_t* seg2, int nmax, float* ring, int32_t* total, int32_t* cnt,
-                         int32_t* fill, int32_t* first, int32_t* snapsz, uint32_t* vflags)
+                         int32_t* seg2, int nmax, float* ring, float* rnoise, float sn2,
+                         int32_t* total, int32_t* cnt, int32_t* fill, int32_t* first,
+                         int32_t* snapsz, uint32_t* vflags)
 {
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -239,6 +240,7 @@ __global__ void k_append(const float* xyz, const int32_t* counters, const int32_
         dst[0] = xyz[3 * src + 0];
         dst[1] = xyz[3 * src + 1];
         dst[2] = xyz[3 * src + 2];
+        if (rnoise) rnoise[(int64_t)s * nmax + slotpos] = sn2;  // the sensor's variance
     }
     __syncwarp();
     if (lane == 0) {
@@ -258,7 +260,9 @@ __global__ void k_snap(int32_t* counters, const int32_t* touched, const uint64_t
                        const int32_t* total, const int32_t* snapsz, int64_t* snapoff,
                        const float* ring, int nmax, int64_t cap, float size, float lam,
                        float sf2, float sn2, float* snap, int64_t* okeys, float* centres,
-                       float* olam, float* osf2, float* osn2, uint32_t* vflags)
+                       float* olam, float* osf2, float* osn2, uint32_t* vflags,
+                       const float* rnoise, const uint8_t* vstate, int tau, float* snoise,
+                       int32_t* ssrc, uint8_t* rtype, uint8_t* rskip)
 {
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -281,10 +285,21 @@ __global__ void k_snap(int32_t* counters, const int32_t* touched, const uint64_t
         const float* p = ring + ((int64_t)s * nmax + src) * 3;
         float* d = snap + (o + k) * 3;
         d[0] = p[0]; d[1] = p[1]; d[2] = p[2];
+        if (rnoise) {
+            const int64_t r = (int64_t)s * nmax + src;
+            snoise[o + k] = rnoise[r];
+            ssrc[o + k] = (int32_t)r;
+        }
     }
     __syncwarp();
     if (lane == 0) {
         snapoff[t] = o;
+        if (rnoise) {  // voxel type before this scan's solve (Sec. 3.3)
+            const int st = vstate[s];
+            const int ty = st == 3 ? 3 : (st == 2 ? 2 : (n >= tau ? 1 : 0));
+            rtype[t] = (uint8_t)ty;
+            rskip[t] = ty == 3 ? 1 : 0;
+        }
         const uint64_t key = keys[s];
         okeys[t] = (int64_t)key;
         for (int a = 0; a < 3; ++a)
@@ -326,6 +341,63 @@ __global__ void k_copy_rows(const int32_t* counters, const int64_t* keys, const 
         for (int a = 0; a < 3; ++a) ocentres[3 * t + a] = centres[3 * t + a];
 }
 
+// one warp per row: variance feedback and the type transition of Sec. 3.3
+__global__ void k_feedback(const int32_t* counters, const int32_t* touched,
+                           const int64_t* snapoff, const uint32_t* status, const float* var,
+                           int GG, const float* spvar, const int32_t* ssrc, float floor_,
+                           float eta_sf2, const uint8_t* rtype, float* rnoise, uint8_t* vstate,
+                           uint8_t* rafter)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= counters[0]) return;
+    const uint32_t st = status[t];
+    const int before = rtype[t];
+    const bool solved = (st & (gpv::VOX_BELOW_TAU | gpv::VOX_NOT_SPD | gpv::VOX_TOO_LARGE |
+                               gpv::VOX_CONVERGED)) == 0;
+    if (!solved) {
+        if (lane == 0)
+            rafter[t] = (st & gpv::VOX_CONVERGED) ? 3 : ((st & gpv::VOX_BELOW_TAU) && before < 2 ? 0 : before);
+        return;
+    }
+    const int64_t o = snapoff[t], e = snapoff[t + 1];
+    for (int64_t k = o + lane; k < e; k += 32) rnoise[ssrc[k]] = fmaxf(spvar[k], floor_);
+    float acc = 0.f;
+    for (int q = lane; q < GG; q += 32) acc += var[(int64_t)t * GG + q];
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    if (lane == 0) {
+        const int after = __fdiv_rn(acc, (float)GG) <= eta_sf2 ? 3 : 2;
+        vstate[touched[t]] = (uint8_t)after;
+        rafter[t] = (uint8_t)after;
+    }
+}
+
+__global__ void k_copy_types(const int32_t* counters, const uint8_t* rtype, const uint8_t* rafter,
+                             uint8_t* before, uint8_t* after)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= counters[0]) return;
+    if (before) before[t] = rtype[t];
+    if (after) after[t] = rafter[t];
+}
+
+__global__ void k_type_counts(const uint64_t* keys, const int32_t* total, const uint8_t* vstate,
+                              uint32_t H, int nmax, int tau, unsigned long long* counts)
+{
+    __shared__ unsigned long long c[4];
+    if (threadIdx.x < 4) c[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < H && keys[i] != kEmpty) {
+        const int n = total[i] < nmax ? total[i] : nmax;
+        const int st = vstate ? vstate[i] : 0;
+        atomicAdd(&c[st == 3 ? 3 : (st == 2 ? 2 : (n >= tau ? 1 : 0))], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], c[threadIdx.x]);
+}
+
 size_t slot_bytes(const gp_voxels_config* c, int64_t cap)
 {
     const size_t P = (size_t)c->max_scan_points, V = (size_t)c->max_scan_voxels;
@@ -334,6 +406,7 @@ size_t slot_bytes(const gp_voxels_config* c, int64_t cap)
     b += V * 4 * 4 + (V + 1) * 4 + (V + 2) * 8 + V * 8 + V * 12 + V * 12 + V * 4;
     b += (size_t)cap * 12;
     b += (kScanBlock + 1) * 12 + 64;
+    if (c->eta > 0.f) b += (size_t)cap * 12 + V * 3;  // feedback: noise, source, pvar; types
     return b;
 }
 
@@ -349,6 +422,7 @@ size_t store_bytes(const gp_voxels_config* c)
     if (!c || c->hash_capacity == 0) return 0;
     const size_t H = c->hash_capacity;
     size_t b = H * (8 + 4 * 5) + H * (size_t)c->max_points * 12 + 64;
+    if (c->eta > 0.f) b += H * (size_t)c->max_points * 4 + H;  // point noise, voxel state
     b += (size_t)(c->scan_slots > 0 ? c->scan_slots : 0) * slot_bytes(c, snap_cap_of(c));
     return b;
 }
@@ -358,6 +432,7 @@ void store_destroy(gpv_store* s)
     if (!s) return;
     cudaFree(s->keys); cudaFree(s->total); cudaFree(s->cnt); cudaFree(s->fill);
     cudaFree(s->first); cudaFree(s->tmap); cudaFree(s->ring); cudaFree(s->nvox);
+    cudaFree(s->rnoise); cudaFree(s->vstate);
     if (s->slots) {
         for (int i = 0; i < s->nslots; ++i) {
             gpv_scan_slot& S = s->slots[i];
@@ -366,12 +441,15 @@ void store_destroy(gpv_store* s)
             cudaFree(S.snapoff); cudaFree(S.keys); cudaFree(S.centres); cudaFree(S.lam);
             cudaFree(S.sf2); cudaFree(S.sn2); cudaFree(S.vflags); cudaFree(S.snap);
             cudaFree(S.scan_tmp); cudaFree(S.scan_tmp64); cudaFree(S.counters); cudaFree(S.npoints);
+            cudaFree(S.snap_noise); cudaFree(S.snap_src); cudaFree(S.snap_pvar);
+            cudaFree(S.rtype); cudaFree(S.rskip); cudaFree(S.rafter);
             if (S.free_ev) cudaEventDestroy(S.free_ev);
             if (S.ins_ev) cudaEventDestroy(S.ins_ev);
         }
         delete[] s->slots;
     }
     if (s->ev_insert) cudaEventDestroy(s->ev_insert);
+    if (s->ev_fb) cudaEventDestroy(s->ev_fb);
     delete s;
 }
 
@@ -407,6 +485,11 @@ int store_create(const gp_voxels_config* c, gpv_store** out, size_t* bytes_acc)
     al((void**)&s->tmap, H * 4);
     al((void**)&s->ring, H * (size_t)s->nmax * 12);
     al((void**)&s->nvox, 4);
+    s->feedback = c->eta > 0.f;
+    if (s->feedback) {
+        al((void**)&s->rnoise, H * (size_t)s->nmax * 4);
+        al((void**)&s->vstate, H);
+    }
     s->slots = new (std::nothrow) gpv_scan_slot[s->nslots];
     if (!s->slots) ok = false;
     for (int i = 0; ok && i < s->nslots; ++i) {
@@ -423,10 +506,18 @@ int store_create(const gp_voxels_config* c, gpv_store** out, size_t* bytes_acc)
         al((void**)&S.scan_tmp64, (kScanBlock + 1) * 8);
         al((void**)&S.counters, 4 * 4);
         al((void**)&S.npoints, 8);
+        if (s->feedback) {
+            const size_t sc = (size_t)(s->snap_cap > 0 ? s->snap_cap : 1);
+            al((void**)&S.snap_noise, sc * 4); al((void**)&S.snap_src, sc * 4);
+            al((void**)&S.snap_pvar, sc * 4);
+            al((void**)&S.rtype, V); al((void**)&S.rskip, V); al((void**)&S.rafter, V);
+        }
         if (ok && cudaEventCreateWithFlags(&S.free_ev, cudaEventDisableTiming) != cudaSuccess) ok = false;
         if (ok && cudaEventCreateWithFlags(&S.ins_ev, cudaEventDisableTiming) != cudaSuccess) ok = false;
     }
     if (ok && cudaEventCreateWithFlags(&s->ev_insert, cudaEventDisableTiming) != cudaSuccess) ok = false;
+    if (ok && cudaEventCreateWithFlags(&s->ev_fb, cudaEventDisableTiming) != cudaSuccess) ok = false;
+    if (ok && s->feedback && cudaMemset(s->vstate, 0, H) != cudaSuccess) ok = false;
     if (ok) {
         const int blk = 256;
         const int grd = (int)((H + blk - 1) / blk);
@@ -473,15 +564,47 @@ cudaError_t store_insert(gpv_store* st, int si, const float* d_xyz, int npts, cu
                                 st->cnt);
     const int wblk = 256, grdw = (V * 32 + wblk - 1) / wblk;
     k_append<<<grdw, wblk, 0, s>>>(d_xyz, S.counters, S.touched, S.segsz, S.segoff, S.seg, S.seg2,
-                                   st->nmax, st->ring, st->total, st->cnt, st->fill, st->first,
-                                   S.snapsz, S.vflags);
+                                   st->nmax, st->ring, st->rnoise, c->sn2, st->total, st->cnt,
+                                   st->fill, st->first, S.snapsz, S.vflags);
     // V + 1 outputs: snapoff[rows] is the total (entries at or past rows scan as zero)
     if ((e = excl_scan<int64_t>(S.snapsz, V + 1, S.counters, S.snapoff, S.scan_tmp64, S.npoints, s)) != cudaSuccess)
         return e;
     const int grdw2 = ((V + 1) * 32 + wblk - 1) / wblk;
     k_snap<<<grdw2, wblk, 0, s>>>(S.counters, S.touched, st->keys, st->total, S.snapsz, S.snapoff,
                                   st->ring, st->nmax, st->snap_cap, st->size, c->lambda, c->sf2,
-                                  c->sn2, S.snap, S.keys, S.centres, S.lam, S.sf2, S.sn2, S.vflags);
+                                  c->sn2, S.snap, S.keys, S.centres, S.lam, S.sf2, S.sn2, S.vflags,
+                                  st->rnoise, st->vstate, c->tau, S.snap_noise, S.snap_src,
+                                  S.rtype, S.rskip);
+    return cudaGetLastError();
+}
+
+cudaError_t store_feedback(gpv_store* st, int si, const uint32_t* status, const float* var,
+                           const gp_voxels_config* c, cudaStream_t s)
+{
+    gpv_scan_slot& S = st->slots[si];
+    const int wblk = 256, grdw = (st->max_vox * 32 + wblk - 1) / wblk;
+    k_feedback<<<grdw, wblk, 0, s>>>(S.counters, S.touched, S.snapoff, status, var,
+                                     c->grid_side * c->grid_side, S.snap_pvar, S.snap_src,
+                                     c->noise_floor, c->eta * c->sf2, S.rtype, st->rnoise,
+                                     st->vstate, S.rafter);
+    return cudaGetLastError();
+}
+
+cudaError_t store_copy_types(gpv_store* st, int si, uint8_t* before, uint8_t* after,
+                             cudaStream_t s)
+{
+    gpv_scan_slot& S = st->slots[si];
+    const int blk = 256, grd = (st->max_vox + blk - 1) / blk;
+    k_copy_types<<<grd, blk, 0, s>>>(S.counters, S.rtype, S.rafter, before, after);
+    return cudaGetLastError();
+}
+
+cudaError_t store_type_counts(gpv_store* st, int tau, unsigned long long* d_counts, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d_counts, 0, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int blk = 256, grd = (int)((st->H + blk - 1) / blk);
+    k_type_counts<<<grd, blk, 0, s>>>(st->keys, st->total, st->vstate, st->H, st->nmax, tau, d_counts);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libgp_voxels.so")
 
 GPV_OK, GPV_EINVAL, GPV_ENOMEM, GPV_EBUDGET, GPV_ECUDA, GPV_ETIMEOUT, GPV_EFULL = 0, -1, -2, -3, -4, -5, -6
 VOX_OK, VOX_BELOW_TAU, VOX_ESCALATED, VOX_NOT_SPD, VOX_TRUNCATED, VOX_TOO_LARGE = 0, 1, 2, 4, 8, 16
+VOX_CONVERGED = 32
+TYPE_A, TYPE_B, TYPE_C, TYPE_D = 0, 1, 2, 3  # voxel types of Sec. 3.3
 PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 SOLVE_ONE_PER_LAUNCH = 1
 
@@ -25,7 +27,8 @@ EXPORTED = [
     "gp_voxels_init_gaussians", "gp_voxels_query_sizes", "gp_voxels_strerror",
     "gp_voxels_last_error", "gp_voxels_insert_scan", "gp_voxels_solve", "gp_voxels_scan_info",
     "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
-    "gp_voxels_last_launches", "gp_voxels_autotune",
+    "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
+    "gp_voxels_scan_types", "gp_voxels_type_counts",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -52,6 +55,8 @@ class gp_voxels_config(ctypes.Structure):
         ("lambda_", ctypes.c_float),
         ("sf2", ctypes.c_float),
         ("sn2", ctypes.c_float),
+        ("eta", ctypes.c_float),
+        ("noise_floor", ctypes.c_float),
     ]
 
 
@@ -97,6 +102,11 @@ def lib() -> ctypes.CDLL:
         L.gp_voxels_last_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_autotune.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P, P, P, P, P, P,
                                          P, P, ctypes.POINTER(ctypes.c_int32)]
+        # h, xyz, offsets, nvox, centres, lam, sf2, sn2, noise, axis, mean, var, status,
+        # pos, scale, quat, pvar, flags, stream
+        L.gp_voxels_solve_csr_noise.argtypes = [P, P, P, ctypes.c_int32] + [P] * 13 + [U32, P]
+        L.gp_voxels_scan_types.argtypes = [P, ctypes.c_int32, P, P, P]
+        L.gp_voxels_type_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -164,6 +174,32 @@ def gp_voxels_solve_csr(h, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, mea
                                    _ptr(var), _ptr(status), _ptr(pos), _ptr(scale), _ptr(quat),
                                    int(flags), _stream(stream))
     _check("gp_voxels_solve_csr", rc)
+
+
+def gp_voxels_solve_csr_noise(h, xyz, offsets, nvox, centres, lam, sf2, sn2, noise, axis, mean,
+                              var, status, pos=None, scale=None, quat=None, pvar=None, flags=0,
+                              stream=None) -> None:
+    """Voxel-GPR with a noise variance per point (None: sn2 of its voxel) and, optionally,
+    the posterior variance at every input point (Sec. 3.3 variance feedback)."""
+    rc = lib().gp_voxels_solve_csr_noise(h, _ptr(xyz), _ptr(offsets), int(nvox), _ptr(centres),
+                                         _ptr(lam), _ptr(sf2), _ptr(sn2), _ptr(noise),
+                                         _ptr(axis), _ptr(mean), _ptr(var), _ptr(status),
+                                         _ptr(pos), _ptr(scale), _ptr(quat), _ptr(pvar),
+                                         int(flags), _stream(stream))
+    _check("gp_voxels_solve_csr_noise", rc)
+
+
+def gp_voxels_scan_types(h, slot, before=None, after=None, stream=None) -> None:
+    """Voxel types (TYPE_A..TYPE_D) of a solved slot's rows before and after its solve."""
+    rc = lib().gp_voxels_scan_types(h, int(slot), _ptr(before), _ptr(after), _stream(stream))
+    _check("gp_voxels_scan_types", rc)
+
+
+def gp_voxels_type_counts(h) -> list[int]:
+    """Stored voxels of each type (a)-(d); synchronises the device."""
+    c = (ctypes.c_int64 * 4)()
+    _check("gp_voxels_type_counts", lib().gp_voxels_type_counts(h, c))
+    return [int(x) for x in c]
 
 
 def gp_voxels_solve_csr_noalloc(cfg, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, mean,

@@ -5,7 +5,9 @@ admitted as soon as it has arrived and one of the handle's scan slots is free; t
 are the memory reserved under the configured budget, so admission is by memory.  Each
 admitted scan runs on its own CUDA stream: host-to-device copy of its points, ALG.STORE
 into the resident voxel hash (the library orders inserts by call order), the Voxel-GPR
-re-solve of the visited voxels and the fused Gaussian initialisation.  Work of scans in
+re-solve of the visited voxels and the fused Gaussian initialisation.  With the voxel
+state machine of Sec. 3.3 on (eta > 0) the library orders each insert after the previous
+scan's solve, since a voxel's type and its points' noise come from that solve.  Work of scans in
 flight overlaps on the device.  The latency of a scan is the time from its arrival to the
 completion of its last queued GPU operation.
 """
@@ -39,6 +41,9 @@ class Lane:
             "keys": torch.empty(V, dtype=torch.int64, device=device),
             "centres": torch.empty(V, 3, dtype=torch.float32, device=device),
         }
+        if cfg.eta > 0:  # voxel types of Sec. 3.3 before and after each solve
+            self.out["type_before"] = torch.empty(V, dtype=torch.uint8, device=device)
+            self.out["type_after"] = torch.empty(V, dtype=torch.uint8, device=device)
         self.done = torch.cuda.Event()
         self.busy = False
         self.scan = -1
@@ -68,6 +73,9 @@ class Server:
             gv.gp_voxels_solve(self.g.h, slot, o["axis"], o["mean"], o["var"], o["status"],
                                o["pos"], o["scale"], o["quat"], o["keys"], o["centres"],
                                lane.stream)
+            if "type_before" in o:
+                gv.gp_voxels_scan_types(self.g.h, slot, o["type_before"], o["type_after"],
+                                        lane.stream)
             if not keep_slot:
                 gv.gp_voxels_release_scan(self.g.h, slot, lane.stream)
             lane.done.record(lane.stream)
@@ -78,7 +86,8 @@ class Server:
         ng = self.cfg.n_s * self.cfg.n_s
         o = lane.out
         res = {k: o[k][:rows].cpu().numpy() for k in ("axis", "mean", "var", "status", "keys",
-                                                       "centres")}
+                                                       "centres", "type_before", "type_after")
+               if k in o}
         for k in ("pos", "scale", "quat"):
             res[k] = o[k][:rows * ng].cpu().numpy()
         res.update(rows=rows, points=npts, flags=flags)

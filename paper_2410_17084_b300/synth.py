@@ -177,6 +177,15 @@ def stress_batch(nvox: int = 1000000, seed: int = 4, axes: str = "random") -> Vo
                      ell=ell, sd=sd)
 
 
+def point_noise(b: VoxelBatch, seed: int, lo: float = 0.1, hi: float = 10.0) -> np.ndarray:
+    """Per-point noise variances for a batch: each point's voxel sn2 times a log-uniform
+    factor on [lo, hi] (the spread of fed-back variances around the sensor's)."""
+    rng = np.random.default_rng(seed)
+    per_pt = np.repeat(b.sn2.astype(np.float64), b.counts)
+    f = np.exp(rng.uniform(np.log(lo), np.log(hi), per_pt.shape[0]))
+    return (per_pt * f).astype(np.float32)
+
+
 # ---------------------------------------------------------------------------
 # Spinning-LiDAR scans for the serving loop
 # ---------------------------------------------------------------------------
