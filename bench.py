@@ -180,23 +180,36 @@ def run_reference(args, rank, world):
 
 
 def cpu_baseline_leg(b, budget_s=12.0) -> dict:
+    """The oracle (GPR + Gaussian init) on all host cores over a bounded sample: a prefix
+    of the workload sized from a probe, or whole passes over it until about budget_s."""
     from oracle import oracle as O
     ncpu = os.cpu_count() or 1
-    probe = b.subset(np.arange(300))
+
+    def one(sub):
+        r = O.solve_batch(sub.xyz, sub.offsets, sub.centres, sub.lam, sub.sf2, sub.sn2, b.size,
+                          b.G, b.tau, nthreads=ncpu)
+        O.init_batch(r["mean"], r["var"], r["axis"], sub.centres, sub.sf2, b.size, b.G, b.n_s,
+                     b.n_r)
+
+    probe = b.subset(np.arange(min(b.nvox, 2000)))
     t = time.perf_counter()
-    O.solve_batch(probe.xyz, probe.offsets, probe.centres, probe.lam, probe.sf2, probe.sn2,
-                  b.size, b.G, b.tau, nthreads=ncpu)
-    per = (time.perf_counter() - t) / 300
-    k = int(min(b.nvox, max(300, budget_s / max(per, 1e-9))))
-    sub = b.subset(np.arange(k))
+    one(probe)
+    per = (time.perf_counter() - t) / probe.nvox
+    k = int(min(b.nvox, max(probe.nvox, budget_s / max(per, 1e-9))))
+    sub = b if k == b.nvox else b.subset(np.arange(k))
+    done, passes = 0, 0
     t = time.perf_counter()
-    r = O.solve_batch(sub.xyz, sub.offsets, sub.centres, sub.lam, sub.sf2, sub.sn2, b.size, b.G,
-                      b.tau, nthreads=ncpu)
-    O.init_batch(r["mean"], r["var"], r["axis"], sub.centres, sub.sf2, b.size, b.G, b.n_s, b.n_r)
-    dt = time.perf_counter() - t
-    return {"value": k / dt, "unit": "voxel solves/s", "cores": ncpu, "kind": "oracle",
-            "sample": f"first {k} of {b.nvox} voxels of the workload (GPR + Gaussian init)",
-            "seconds": dt}
+    while True:
+        one(sub)
+        done += k
+        passes += 1
+        dt = time.perf_counter() - t
+        if dt >= 0.8 * budget_s or k < b.nvox or passes >= 20:
+            break
+    what = (f"first {k} of {b.nvox} voxels" if k < b.nvox
+            else f"all {b.nvox} voxels x {passes} pass(es)")
+    return {"value": done / dt, "unit": "voxel solves/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"{what} of the workload (GPR + Gaussian init)", "seconds": dt}
 
 
 def run_extras(b, d, stream, timed) -> dict:
