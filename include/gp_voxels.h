@@ -303,8 +303,10 @@ GPV_API int gp_voxels_solve_csr_noalloc(const gp_voxels_config* cfg, const float
 GPV_API int gp_voxels_query_sizes(const gp_voxels_config* cfg, size_t* bytes_out);
 
 /* Autotuner of the batched solve (the paper has no counterpart; its batch is a library
- * call): runs every size bucket of this batch with each candidate CTA size (256 and 512
- * threads; persistent grids sized by occupancy) and keeps the fastest per bucket in the
+ * call): runs every size bucket of this batch with each candidate CTA size (128, 256 and
+ * 512 threads, at least the bucket's largest n for shared-memory factors) and factor
+ * variant (blocked or per-column, shared-memory buckets), persistent grids sized by
+ * occupancy, and keeps the fastest per bucket in the
  * handle for later solves of any batch.  Inputs and outputs as gp_voxels_solve_csr (the
  * outputs are overwritten with scratch results; the FP64 escalation is not run).
  * Synchronises `stream`.  *h_changed = buckets whose choice changed.

@@ -37,6 +37,7 @@ struct Bucket {
     int smem;      // dynamic shared memory of its launch
     int grid;      // persistent CTAs
     bool tri_smem; // factor in shared memory (else in the global workspace slice)
+    bool percol;   // per-column (not blocked) factor and inverse
 };
 
 struct PrecPlan {
@@ -145,6 +146,7 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         B.tri_smem = B.hi <= P.nmax_smem;
         // the workspace variant lays out its slice for max_points, whatever the bucket
         B.nthr = solve_threads(B.hi, B.tri_smem);
+        B.percol = B.tri_smem && B.hi <= default_percol_max(tsize(kind));
         const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
                                       tsize(kind), B.tri_smem, B.nthr);
         if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) return GPV_EINVAL;  // panels too thin
@@ -427,6 +429,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
                 if (n <= P.b[k].hi) { b = k; break; }
             const Bucket& B = P.b[b];
             a.nmax = B.tri_smem ? B.hi : c.max_points;
+            a.percol_max = B.percol ? B.hi : 0;
             CK(launch_solve(kind, B.tri_smem, B.nthr, a, 1, B.smem, s));
             ++h->last_launches;
         }
@@ -448,6 +451,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_count = x.d_bcount + b;
         a.work_next = x.d_next + b;
         a.nmax = B.tri_smem ? B.hi : c.max_points;
+        a.percol_max = B.percol ? B.hi : 0;
         CK(launch_solve(kind, B.tri_smem, B.nthr, a, B.grid, B.smem, ss));
         ++h->last_launches;
         used |= 1 << (si % kNumBuckets);
@@ -466,6 +470,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_count = x.d_esc_count;
         a.work_next = x.d_next + P.nb;
         a.nmax = a.nmax_small_f64;
+        a.percol_max = default_percol_max(8);
         CK(launch_solve(PREC_F64, true, solve_threads(a.nmax, true), a, h->esc_grid_small,
                         h->esc_smem_small, s));
         ++h->last_launches;
@@ -684,13 +689,18 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     int changed = 0;
-    const int cand[2] = {256, 512};
+    const int cand[3] = {128, 256, 512};
     for (int b = 0; b < P.nb; ++b) {
         Bucket& B = P.b[b];
         float best_ms = 3.0e38f;
         int best = B.nthr, best_smem = B.smem, best_grid = B.grid;
-        for (int ci = 0; ci < 2; ++ci) {
-            const int nt = cand[ci];
+        bool best_pc = B.percol;
+        for (int ci = 0; ci < 6; ++ci) {
+            const int nt = cand[ci % 3];
+            const bool pc = ci >= 3;  // per-column variant: shared-memory buckets only
+            if (pc && !B.tri_smem) continue;
+            if (B.tri_smem && nt < B.hi) continue;  // the shared-memory variants need n <= CTA size
+            if (!B.tri_smem && nt < 256) continue;
             const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
                                           tsize(kind), B.tri_smem, nt);
             if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) continue;
@@ -703,6 +713,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
             a.work_count = x.d_bcount + b;
             a.work_next = x.d_next + b;
             a.nmax = B.tri_smem ? B.hi : c.max_points;
+            a.percol_max = pc ? B.hi : 0;
             float ms = 3.0e38f;
             for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel
                 CK(cudaMemsetAsync(x.d_next + b, 0, sizeof(int32_t), s));
@@ -714,9 +725,12 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
                 CK(cudaEventElapsedTime(&t, e0, e1));
                 ms = std::min(ms, t);
             }
-            if (ms < best_ms) { best_ms = ms; best = nt; best_smem = sp.total; best_grid = grid; }
+            if (ms < best_ms) {
+                best_ms = ms; best = nt; best_smem = sp.total; best_grid = grid; best_pc = pc;
+            }
         }
-        if (best != B.nthr) ++changed;
+        if (best != B.nthr || best_pc != B.percol) ++changed;
+        B.percol = best_pc;
         B.nthr = best;
         B.smem = best_smem;
         B.grid = best_grid;

@@ -63,6 +63,7 @@ struct SolveArgs {
     int nmax;            // largest n handled by this launch
     int max_points;      // voxels with more points are reported VOX_TOO_LARGE
     int nmax_small_f64;  // escalated voxels up to this n take the shared-memory FP64 pass
+    int percol_max;      // shared-memory voxels up to this n use the per-column factor/inverse
 };
 
 // Shared-memory plan of one CTA (bytes), identical on host and device.
@@ -127,10 +128,13 @@ __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize
 // Text of a CUDA error for gp_voxels_last_error() (gpv_api.cu)
 void gpv_record_cuda_error(cudaError_t e);
 
-// CTA size of a launch: small voxels are bound by the latency of their per-column
-// barriers and gain from two CTAs per SM; from 128 points on (and for the workspace
-// variant) shared memory allows one CTA per SM, which then gets 16 warps.
+// Default CTA size of a launch: small voxels are bound by the latency of their barriers
+// and gain from several CTAs per SM; from 128 points on (and for the workspace variant)
+// shared memory allows one CTA per SM, which then gets 16 warps.  The shared-memory
+// variants need n <= CTA size.  gp_voxels_autotune may choose another per bucket.
 inline int solve_threads(int nmax, bool tri_in_smem) { return (!tri_in_smem || nmax >= 128) ? 512 : 256; }
+// Default per-column (rather than blocked) factor and inverse: 8-byte types up to 96 points.
+inline int default_percol_max(int tsize) { return tsize == 8 ? 96 : 0; }
 
 // Launchers (gpv_solve.cu)
 cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, int32_t* bcount,

@@ -177,6 +177,7 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
         a.work_count = scr + kOffCount + b;
         a.work_next = scr + kOffNext + b;
         a.nmax = bnd.hi[b];
+        a.percol_max = bnd.hi[b] <= default_percol_max(kind == PREC_F32 ? 4 : 8) ? bnd.hi[b] : 0;
         if ((e = launch_solve(kind, true, nt, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
     }
     if (kind == PREC_FF) {  // FP64 re-solve of the voxels that failed the conditioning check
@@ -192,6 +193,7 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
         a.work_count = scr + kOffEscCount;
         a.work_next = scr + kOffNext + nb;
         a.nmax = a.nmax_small_f64;
+        a.percol_max = default_percol_max(8);
         if ((e = launch_solve(PREC_F64, true, nt, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
     }
     return GPV_OK;

@@ -87,6 +87,51 @@ __device__ __forceinline__ ff shfl_idx(ff x, int src)
     return ff_make(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
 }
 
+// Rank-pw update of the trailing triangle (rows and columns p1..n-1) with the panel
+// columns p0..p0+pw-1, in TS x TS register tiles (tile t -> block row bi >= block column bj).
+template <class T, int TS>
+__device__ __forceinline__ void trail_update(T* L, int n, int p0, int pw, int p1)
+{
+    const int m = n - p1;
+    const int mb = (m + TS - 1) / TS;
+    const int ntiles = mb * (mb + 1) / 2;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        int bi = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+        while (bi > 0 && bi * (bi + 1) / 2 > t) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bj = t - bi * (bi + 1) / 2;
+        const int i0 = p1 + TS * bi, j0 = p1 + TS * bj;
+        T acc[TS][TS];
+#pragma unroll
+        for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int w = 0; w < TS; ++w) acc[u][w] = zero<T>();
+        for (int c = 0; c < pw; ++c) {
+            const T* col = L + tri_off(p0 + c, n) - (p0 + c);  // col[r] = L(r, p0 + c)
+            T li[TS], lj[TS];
+#pragma unroll
+            for (int u = 0; u < TS; ++u) {
+                li[u] = col[min(i0 + u, n - 1)];
+                lj[u] = col[min(j0 + u, n - 1)];
+            }
+#pragma unroll
+            for (int u = 0; u < TS; ++u)
+#pragma unroll
+                for (int w = 0; w < TS; ++w) acc_fma(acc[u][w], li[u], lj[w]);
+        }
+#pragma unroll
+        for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int w = 0; w < TS; ++w) {
+                const int i = i0 + u, j = j0 + w;
+                if (i < n && j <= i) {
+                    T* p = L + tri_off(j, n) + (i - j);
+                    *p = *p - acc_norm(acc[u][w]);
+                }
+            }
+    }
+}
+
 // Right-looking Cholesky by panels of 16 columns, in place in the packed triangle:
 // (a) the 16 x 16 diagonal block is factored by warp 0 in registers (lane r holds row r,
 //     updates exchanged by shuffles); (b) the rows below the block solve against it, one
@@ -165,45 +210,14 @@ __device__ bool chol_smem(T* L, int n, T* ild, float* s_dm, int* s_fail)
                 if (c < pw) L[tri_off(p0 + c, n) + (i - p0 - c)] = a[c];
         }
         __syncthreads();
-        const int m = n - p1;  // (c) trailing triangle, 4 x 4 tiles
+        const int m = n - p1;  // (c) trailing triangle in 4 x 4 tiles, 2 x 2 when few
         if (m > 0) {
-            const int mb = (m + 3) >> 2;
-            const int ntiles = mb * (mb + 1) / 2;
-            for (int t = tid; t < ntiles; t += nthr) {
-                int bi = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
-                while (bi > 0 && bi * (bi + 1) / 2 > t) --bi;
-                while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-                const int bj = t - bi * (bi + 1) / 2;
-                const int i0 = p1 + 4 * bi, j0 = p1 + 4 * bj;
-                T acc[4][4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) acc[u][w] = zero<T>();
-                for (int c = 0; c < pw; ++c) {
-                    const T* col = L + tri_off(p0 + c, n) - (p0 + c);  // col[r] = L(r, p0 + c)
-                    T li[4], lj[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        li[u] = col[min(i0 + u, n - 1)];
-                        lj[u] = col[min(j0 + u, n - 1)];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) acc_fma(acc[u][w], li[u], lj[w]);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const int i = i0 + u, j = j0 + w;
-                        if (i < n && j <= i) {
-                            T* p = L + tri_off(j, n) + (i - j);
-                            *p = *p - acc_norm(acc[u][w]);
-                        }
-                    }
-            }
+            // rounds of tiles per thread x products per tile: the smaller wins
+            const int mb4 = (m + 3) >> 2, mb2 = (m + 1) >> 1;
+            const int cost4 = (mb4 * (mb4 + 1) / 2 + nthr - 1) / nthr * 16;
+            const int cost2 = (mb2 * (mb2 + 1) / 2 + nthr - 1) / nthr * 4;
+            if (cost4 <= cost2) trail_update<T, 4>(L, n, p0, pw, p1);
+            else trail_update<T, 2>(L, n, p0, pw, p1);
         }
         __syncthreads();
     }
@@ -229,11 +243,15 @@ __device__ void inv_smem(T* L, int n, const T* ild)
 #pragma unroll
             for (int u = 0; u < 4; ++u) y[s][u] = zero<T>();
             const int t = tid + s * nthr;
+            // the lanes of a warp run the k loop in step from the warp's smallest column
+            // (X(k, c) = 0 above the diagonal), so their loads of L are broadcasts
+            const int cw = t < ntask ? t % r0 : r0;
+            const int kbeg = __reduce_min_sync(0xffffffffu, cw);
             if (t < ntask) {
-                const int c = t % r0, g = t / r0;
+                const int c = cw, g = t / r0;
                 const T* xc = L + tri_off(c, n) - c;  // xc[k] = X(k, c)
-                for (int k = c; k < r0; ++k) {
-                    const T x = xc[k];
+                for (int k = kbeg; k < r0; ++k) {
+                    const T x = k >= c ? xc[k] : zero<T>();
                     const T* lk = L + tri_off(k, n) - k + r0;  // lk[r] = L(r0 + r, k)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -651,7 +669,7 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         if (!ok && tid == 0) s_fail = 1;
         __syncthreads();
     } else {
-        if (sizeof(T) == 8 && n <= 96) {
+        if (n <= A.percol_max) {
             chol_percol_smem<T>(L, n, dmin, dmax, s_fail);
         } else {
             __shared__ float s_dm[2];
@@ -699,7 +717,7 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     if (!TRI_SMEM) big_invert<T>(L, n, W, P.rb);
     // ---- A4': X = L^-1 in place (blocked by rows, see inv_smem) ---------------------
     if (TRI_SMEM) {
-        if (sizeof(T) == 8 && n <= 96) inv_percol_smem<T>(L, n);
+        if (n <= A.percol_max) inv_percol_smem<T>(L, n);
         else inv_smem<T>(L, n, tmp);
     }
     __syncthreads();
@@ -859,8 +877,9 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     __syncthreads();
 }
 
+// At most 128 registers per thread at every CTA size, so that 512 threads fit an SM.
 template <class T, bool TRI_SMEM, int NT>
-__global__ void __launch_bounds__(NT) k_solve(SolveArgs A)
+__global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[6 * 32];
@@ -976,6 +995,7 @@ template <class T, bool S>
 static cudaError_t launch_t(int nthr, const SolveArgs& a, int grid, int smem, cudaStream_t s)
 {
     if (nthr == 512) k_solve<T, S, 512><<<grid, 512, smem, s>>>(a);
+    else if (nthr == 128) k_solve<T, S, 128><<<grid, 128, smem, s>>>(a);
     else k_solve<T, S, 256><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -1010,7 +1030,8 @@ cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out)
 template <class T, bool S>
 static const void* kfun(int nthr)
 {
-    return nthr == 512 ? (const void*)k_solve<T, S, 512> : (const void*)k_solve<T, S, 256>;
+    return nthr == 512 ? (const void*)k_solve<T, S, 512>
+                       : (nthr == 128 ? (const void*)k_solve<T, S, 128> : (const void*)k_solve<T, S, 256>);
 }
 
 cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm)
