@@ -393,6 +393,79 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
+/* Full posterior covariance of the query nodes (Eq. 3, Sigma* of the  */
+/* supplementary Alg. 3): cov[q][q'] = k(x*_q, x*_q') - k_q^T A^-1 k_q' */
+/* with A = K + sn2 I, evaluated from its definition through z_q =     */
+/* L^-1 k_q: cov[q][q'] = k(x*_q, x*_q') - z_q . z_q'.  mean as in     */
+/* gpo_solve_voxel.  cov is G^2 x G^2 row-major.                       */
+/* ------------------------------------------------------------------ */
+int gpo_solve_voxel_fullcov(const float* xyz, int64_t n, const float* centre, double size, int G,
+                            double lambda, double sf2, double sn2, int mean_mode,
+                            int axis_override, int* axis_out, double* mean, double* cov)
+{
+    int axis = axis_override >= 0 ? axis_override : gpo_pca_axis(xyz, n, NULL, NULL);
+    int p1, p2;
+    param_axes(axis, &p1, &p2);
+    *axis_out = axis;
+    const int64_t Q = (int64_t)G * G;
+    double* x1 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* x2 = (double*)malloc(sizeof(double) * (size_t)n);
+    double* fm = (double*)malloc(sizeof(double) * (size_t)n);
+    double* A = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    double* alpha = (double*)malloc(sizeof(double) * (size_t)n);
+    double* k = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Z = (double*)malloc(sizeof(double) * (size_t)n * (size_t)Q);
+    for (int64_t i = 0; i < n; ++i) {
+        x1[i] = (double)xyz[3 * i + p1] - (double)centre[p1];
+        x2[i] = (double)xyz[3 * i + p2] - (double)centre[p2];
+        fm[i] = (double)xyz[3 * i + axis] - (double)centre[axis];
+    }
+    double m = 0.0;
+    if (mean_mode == 1) {
+        for (int64_t i = 0; i < n; ++i) m += fm[i];
+        m /= (double)n;
+    }
+    for (int64_t i = 0; i < n; ++i) fm[i] -= m;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double d1 = x1[i] - x1[j], d2 = x2[i] - x2[j];
+            A[i * n + j] = sf2 * exp(-lambda * (d1 * d1 + d2 * d2)) + (i == j ? sn2 : 0.0);
+        }
+    int status = GPO_OK;
+    if (cholesky(A, n) != 0) {
+        status = GPO_NOT_SPD;
+        goto done;
+    }
+    forward_sub(A, n, fm, y);
+    backward_sub(A, n, y, alpha);
+    for (int64_t q = 0; q < Q; ++q) {
+        double u = grid_node((int)(q / G), G, size), v = grid_node((int)(q % G), G, size);
+        double mu = m;
+        for (int64_t t = 0; t < n; ++t) {
+            double d1 = x1[t] - u, d2 = x2[t] - v;
+            k[t] = sf2 * exp(-lambda * (d1 * d1 + d2 * d2));
+            mu += k[t] * alpha[t];
+        }
+        mean[q] = mu;
+        forward_sub(A, n, k, Z + q * n);
+    }
+    for (int64_t q = 0; q < Q; ++q) {
+        double u = grid_node((int)(q / G), G, size), v = grid_node((int)(q % G), G, size);
+        for (int64_t r = 0; r < Q; ++r) {
+            double u2 = grid_node((int)(r / G), G, size), v2 = grid_node((int)(r % G), G, size);
+            double kk = sf2 * exp(-lambda * ((u - u2) * (u - u2) + (v - v2) * (v - v2)));
+            double zz = 0.0;
+            for (int64_t t = 0; t < n; ++t) zz += Z[q * n + t] * Z[r * n + t];
+            cov[q * Q + r] = kk - zz;
+        }
+    }
+done:
+    free(x1); free(x2); free(fm); free(A); free(y); free(alpha); free(k); free(Z);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* Quaternion (w, x, y, z) of a proper rotation matrix R (row-major), */
 /* the textbook trace/major-diagonal branches; sign fixed to w >= 0.  */
 /* ------------------------------------------------------------------ */

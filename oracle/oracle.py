@@ -55,6 +55,9 @@ def lib():
         _lib.gpo_solve_voxel_hetero.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double, P, ctypes.c_int,
                                                 ctypes.c_int, P, P, P, P]
+        _lib.gpo_solve_voxel_fullcov.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_int, ctypes.c_int, P, P, P]
         _lib.gpo_init_voxel.argtypes = [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, P, P, P, P]
@@ -132,6 +135,21 @@ def solve_voxel_hetero(xyz, centre, size, G, lam, sf2, noise, mean_mode=1, axis_
                                       int(axis_override), ctypes.byref(ax), _p(mean), _p(var),
                                       _p(pvar))
     return st, ax.value, mean, var, pvar
+
+
+def solve_voxel_fullcov(xyz, centre, size, G, lam, sf2, sn2, mean_mode=1, axis_override=-1):
+    """Posterior mean and full G^2 x G^2 covariance Sigma* of the query nodes (Eq. 3,
+    the Sigma* of the supplementary Alg. 3): (status, axis, mean[G*G], cov[G*G, G*G])."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    centre = np.ascontiguousarray(centre, dtype=np.float32).reshape(3)
+    Q = G * G
+    mean = np.zeros(Q)
+    cov = np.zeros((Q, Q))
+    ax = ctypes.c_int(0)
+    st = lib().gpo_solve_voxel_fullcov(_p(xyz), xyz.shape[0], _p(centre), float(size), int(G),
+                                       float(lam), float(sf2), float(sn2), int(mean_mode),
+                                       int(axis_override), ctypes.byref(ax), _p(mean), _p(cov))
+    return st, ax.value, mean, cov
 
 
 def init_voxel(mean, var, axis, centre, size, G, n_s, n_r, sf2, init_mode=0):
