@@ -61,8 +61,10 @@ enum {
     GPV_VOX_NOT_SPD = 4,    /* Gram not positive definite in the final precision */
     GPV_VOX_TRUNCATED = 8,  /* bucket overflowed; oldest points were dropped */
     GPV_VOX_TOO_LARGE = 16, /* n > max_points: not processed; prior written */
-    GPV_VOX_CONVERGED = 32  /* serving with the state machine on: the voxel had
+    GPV_VOX_CONVERGED = 32, /* serving with the state machine on: the voxel had
                                converged (type d, Sec. 3.3), not solved; prior written */
+    GPV_VOX_FAILED = 64     /* a bounded wait of the tensor-core pipeline gave up; the
+                               voxel's outputs are not valid */
 };
 
 /* Arithmetic of the solve. */
@@ -177,6 +179,29 @@ GPV_API int gp_voxels_solve_csr_noise(gp_voxels_t* h, const float* d_xyz,
                               float* d_var, uint32_t* d_status, float* d_pos, float* d_scale,
                               float* d_quat, float* d_pvar, uint32_t flags,
                               gpv_stream_t stream);
+
+/* The paper's own formulation of the solve (supplementary Alg. 3), for comparison and
+ * for the full posterior covariance: ky = K + sigma^2 I, LU with partial pivoting, the
+ * explicit inverse ky^-1, k_k* = K*^T ky^-1, mu* = k_k* f and the FULL
+ * Sigma* = K** - k_k* K* over the G^2 query nodes, all in FP32 as the paper's
+ * single-precision library routines (the last product on the tensor cores as three TF32
+ * products, which keeps FP32-level accuracy).  Value axis, local frame, grid, prior mean
+ * (mean_mode) and kernel as gp_voxels_solve_csr; config precision is ignored.
+ * Inputs as gp_voxels_solve_csr.  Outputs (device, caller-owned):
+ *   d_axis [nvox] u8, d_mean [nvox, G*G], d_status [nvox] (GPV_VOX_* bits),
+ *   d_cov [nvox, G*G, G*G] FP32 row-major: Sigma*(q, q') at d_cov[(v G^2 + q) G^2 + q'].
+ * Voxels below tau, above the size this path holds in one CTA's shared memory (*h_nmax,
+ * about 200 points at G = 16) or whose FP32 LU meets a zero pivot (GPV_VOX_NOT_SPD) get
+ * mean 0 and the prior K**.  FP32 LU and inverse lose about log10(cond(ky)) digits:
+ * on dense voxels the variances are far less accurate than gp_voxels_solve_csr's.
+ * The first call allocates a workspace of about 512 MB (counted against mem_budget) and
+ * synchronises nothing; later calls allocate nothing.  h_nmax (may be NULL) receives the
+ * largest n solved.  Errors: GPV_EINVAL, GPV_EBUDGET, GPV_ENOMEM, GPV_ECUDA. */
+GPV_API int gp_voxels_solve_alg3(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets,
+                                 int32_t nvox, const float* d_centres, const float* d_lambda,
+                                 const float* d_sf2, const float* d_sn2, uint8_t* d_axis,
+                                 float* d_mean, float* d_cov, uint32_t* d_status,
+                                 gpv_stream_t stream, int32_t* h_nmax);
 
 /* Gaussian initialisation from given predictions (Sec. 3.2, Eq. 6-8): for each of the
  * n_s x n_s subgrids of each voxel, weights w = 1 / max(var, 1e-6 sf2), position

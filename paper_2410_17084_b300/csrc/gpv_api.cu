@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/gp_voxels.h"
+#include "gpv_alg3.h"
 #include "gpv_internal.h"
 #include "gpv_store.h"
 
@@ -81,6 +82,13 @@ struct gp_voxels {
     size_t bytes = 0;
     gpv_store* store = nullptr;
     int last_launches = 0;          // kernels queued by the last solve call
+    // workspace of the Alg. 3 formulation (allocated by its first call)
+    struct {
+        int nmax = 0, kp = 0, chunk = 0;
+        float *pb = nullptr, *ps = nullptr, *fa = nullptr, *fb = nullptr;
+        uint32_t* st = nullptr;
+        int32_t* n = nullptr;
+    } a3;
 };
 
 static int prec_kind(int precision)
@@ -238,6 +246,8 @@ static void release(gp_voxels_t* h)
         delete[] h->sctx;
     }
     cudaFree(h->d_one); cudaFree(h->d_ident); cudaFree(h->d_pl_next);
+    cudaFree(h->a3.pb); cudaFree(h->a3.ps); cudaFree(h->a3.fa); cudaFree(h->a3.fb);
+    cudaFree(h->a3.st); cudaFree(h->a3.n);
     store_destroy(h->store);
     delete h;
 }
@@ -517,6 +527,74 @@ extern "C" int gp_voxels_solve_csr_noise(gp_voxels_t* h, const float* d_xyz,
     return gpv_solve_queue(h, h->main, d_xyz, d_offsets, nvox, nullptr, d_centres, d_lambda,
                            d_sf2, d_sn2, d_axis, d_mean, d_var, d_status, d_pos, d_scale, d_quat,
                            flags, (cudaStream_t)stream, d_noise, d_pvar, nullptr);
+}
+
+// Workspace of the Alg. 3 path: k_k* (two TF32 halves) and the K* factors of `chunk`
+// voxels; the chunk is sized to about 512 MB.
+static int alg3_workspace(gp_voxels_t* h)
+{
+    if (h->a3.pb) return GPV_OK;
+    const gp_voxels_config& c = h->cfg;
+    const int G = c.grid_side, Q = G * G;
+    const int nmax = std::min(c.max_points, alg3_max_n(G));
+    if (nmax < c.tau) return GPV_EINVAL;
+    const int kp = (nmax + 31) / 32 * 32;
+    const size_t per = (size_t)2 * Q * kp * 4 + (size_t)2 * kp * G * 4 + 8;
+    int chunk = (int)std::min<size_t>((size_t)c.max_voxels, std::max<size_t>(1, ((size_t)512 << 20) / per));
+    const size_t need = per * (size_t)chunk;
+    if (c.mem_budget && h->bytes + need > c.mem_budget) return GPV_EBUDGET;
+    auto al = [&](void** p, size_t b) -> int {
+        cudaError_t e = cudaMalloc(p, b);
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return GPV_ENOMEM; }
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->bytes += b;
+        return GPV_OK;
+    };
+    int rc;
+    if ((rc = al((void**)&h->a3.pb, (size_t)chunk * Q * kp * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.ps, (size_t)chunk * Q * kp * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.fa, (size_t)chunk * kp * G * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.fb, (size_t)chunk * kp * G * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.st, (size_t)chunk * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.n, (size_t)chunk * 4)) != GPV_OK) return rc;
+    h->a3.nmax = nmax;
+    h->a3.kp = kp;
+    h->a3.chunk = chunk;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_solve_alg3(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets,
+                                    int32_t nvox, const float* d_centres, const float* d_lambda,
+                                    const float* d_sf2, const float* d_sn2, uint8_t* d_axis,
+                                    float* d_mean, float* d_cov, uint32_t* d_status,
+                                    gpv_stream_t stream, int32_t* h_nmax)
+{
+    if (!h || nvox < 0 || nvox > h->cfg.max_voxels) return GPV_EINVAL;
+    int rc = alg3_workspace(h);
+    if (rc != GPV_OK) return rc;
+    if (h_nmax) *h_nmax = h->a3.nmax;
+    if (nvox == 0) return GPV_OK;
+    if (!d_xyz || !d_offsets || !d_centres || !d_lambda || !d_sf2 || !d_sn2 || !d_axis ||
+        !d_mean || !d_cov || !d_status)
+        return GPV_EINVAL;
+    const gp_voxels_config& c = h->cfg;
+    Alg3Args a;
+    memset(&a, 0, sizeof(a));
+    a.xyz = d_xyz; a.offsets = d_offsets; a.centres = d_centres;
+    a.lam = d_lambda; a.sf2 = d_sf2; a.sn2 = d_sn2;
+    a.size = c.voxel_size; a.G = c.grid_side; a.tau = c.tau; a.mean_mode = c.mean_mode;
+    a.nmax = h->a3.nmax; a.kp = h->a3.kp;
+    a.axis = d_axis; a.mean = d_mean; a.cov = d_cov; a.status = d_status;
+    a.ws_pb = h->a3.pb; a.ws_ps = h->a3.ps; a.ws_fa = h->a3.fa; a.ws_fb = h->a3.fb;
+    a.ws_status = h->a3.st; a.ws_n = h->a3.n;
+    h->last_launches = 0;
+    for (int32_t v0 = 0; v0 < nvox; v0 += h->a3.chunk) {
+        a.v0 = v0;
+        int nl = 0;
+        CK(alg3_launch_chunk(a, std::min(h->a3.chunk, nvox - v0), (cudaStream_t)stream, &nl));
+        h->last_launches += nl;
+    }
+    return GPV_OK;
 }
 
 extern "C" int gp_voxels_init_gaussians(gp_voxels_t* h, int32_t nvox, const uint8_t* d_axis,

@@ -16,6 +16,7 @@ enum : uint32_t {
     VOX_TRUNCATED = 8u,
     VOX_TOO_LARGE = 16u,
     VOX_CONVERGED = 32u,
+    VOX_FAILED = 64u,
 };
 
 constexpr int kThreads = 512;   // largest CTA size of the solve kernels

@@ -1,11 +1,13 @@
 // gpv_solve.cu -- batched Voxel-GPR (GS-LIVM Sec. 3.1, Alg. 1, Eq. 2-3) on sm_103a.
 //
 // One CTA solves one voxel at a time and pulls the next voxel from a per-launch work
-// queue (a persistent grid sized to the SM count).  Per voxel, all in shared memory:
-//   A1  PCA of the points (FP64 sums, 3x3 Jacobi) -> value axis (Sec. 3.1)
+// queue (a persistent grid sized to the SM count).  Per voxel, in shared memory (or, for
+// voxels whose factor does not fit, in the CTA's slice of a global workspace):
+//   A1  PCA of the points (FP32, voxel-local) -> value axis (Sec. 3.1)
 //   A2  voxel-local training inputs x (parameter axes) and targets f (value axis)
-//   A3  Gram K + sigma^2 I, packed lower triangle, column-major (Eq. 2)
-//   A4  Cholesky K + sigma^2 I = L L^T, right-looking, one barrier per column
+//   A3  Gram K + D (D = sigma^2 I, or a noise variance per point), packed lower
+//       triangle, column-major (Eq. 2)
+//   A4  Cholesky K + D = L L^T: blocked right-looking (16-column panels) or per column
 //       (replaces the LU + explicit inverse of the paper's Alg. 3)
 //       -> L^-1 in place (n^3/6 more flops buys a barrier-free contraction below)
 //   A5  alpha = L^-T L^-1 (f - m)
@@ -20,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gpv_common.cuh"
 #include "gpv_init.cuh"
 #include "gpv_internal.h"
 #include "gpv_num.cuh"
@@ -28,56 +31,6 @@ namespace gpv {
 
 // column-major packed lower triangle of an n x n matrix: element (r, c), r >= c
 __device__ __forceinline__ int tri_off(int c, int n) { return c * n - ((c * (c - 1)) >> 1); }
-
-__device__ __forceinline__ float shfl_x(float x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
-__device__ __forceinline__ double shfl_x(double x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
-__device__ __forceinline__ ff shfl_x(ff x, int o)
-{
-    return ff_make(__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o));
-}
-
-// Sum of K values of type R over the CTA (fixed order: deterministic); every thread
-// gets the totals.  red must hold K * 32 values of R.
-template <class R, int K>
-__device__ __forceinline__ void block_sum(R (&v)[K], R* red)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] = v[k] + shfl_x(v[k], o);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) red[k * 32 + wid] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        R s = red[k * 32];
-        for (int w = 1; w < nw; ++w) s = s + red[k * 32 + w];
-        v[k] = s;
-    }
-    __syncthreads();
-}
-
-// Value axis of a point set: normal = eigenvector of the smallest eigenvalue of the
-// covariance; axis = argmax |normal_k| with exact ties resolved Z, then X, then Y.
-// The decision needs no more than FP32: voxels whose two largest normal components
-// lie within 1e-3 are axis-ambiguous by definition.
-__device__ inline int value_axis_from_cov(const float c6[6])
-{
-    float ev[3], E[9];
-    sym3_eig<float>(c6, ev, E);
-    int k = 0;
-    if (ev[1] < ev[k]) k = 1;
-    if (ev[2] < ev[k]) k = 2;
-    const float nx = fabsf(E[0 + k]), ny = fabsf(E[3 + k]), nz = fabsf(E[6 + k]);
-    int ax = 2;
-    float best = nz;
-    if (nx > best) { ax = 0; best = nx; }
-    if (ny > best) { ax = 1; }
-    return ax;
-}
 
 // ---- blocked factor and inverse for voxels whose triangle lives in shared memory ----
 __device__ __forceinline__ float shfl_idx(float x, int src) { return __shfl_sync(0xffffffffu, x, src); }

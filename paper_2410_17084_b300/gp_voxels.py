@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libgp_voxels.so")
 
 GPV_OK, GPV_EINVAL, GPV_ENOMEM, GPV_EBUDGET, GPV_ECUDA, GPV_ETIMEOUT, GPV_EFULL = 0, -1, -2, -3, -4, -5, -6
 VOX_OK, VOX_BELOW_TAU, VOX_ESCALATED, VOX_NOT_SPD, VOX_TRUNCATED, VOX_TOO_LARGE = 0, 1, 2, 4, 8, 16
-VOX_CONVERGED = 32
+VOX_CONVERGED, VOX_FAILED = 32, 64
 TYPE_A, TYPE_B, TYPE_C, TYPE_D = 0, 1, 2, 3  # voxel types of Sec. 3.3
 PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 SOLVE_ONE_PER_LAUNCH = 1
@@ -28,7 +28,7 @@ EXPORTED = [
     "gp_voxels_last_error", "gp_voxels_insert_scan", "gp_voxels_solve", "gp_voxels_scan_info",
     "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
     "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
-    "gp_voxels_scan_types", "gp_voxels_type_counts",
+    "gp_voxels_scan_types", "gp_voxels_type_counts", "gp_voxels_solve_alg3",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
         L.gp_voxels_solve_csr_noise.argtypes = [P, P, P, ctypes.c_int32] + [P] * 13 + [U32, P]
         L.gp_voxels_scan_types.argtypes = [P, ctypes.c_int32, P, P, P]
         L.gp_voxels_type_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        L.gp_voxels_solve_alg3.argtypes = [P, P, P, ctypes.c_int32] + [P] * 9 + [
+            ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -187,6 +189,18 @@ def gp_voxels_solve_csr_noise(h, xyz, offsets, nvox, centres, lam, sf2, sn2, noi
                                          _ptr(pos), _ptr(scale), _ptr(quat), _ptr(pvar),
                                          int(flags), _stream(stream))
     _check("gp_voxels_solve_csr_noise", rc)
+
+
+def gp_voxels_solve_alg3(h, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, mean, cov, status,
+                         stream=None) -> int:
+    """The paper's Alg. 3 formulation in FP32 with the full posterior covariance
+    cov [nvox, G*G, G*G]; returns the largest voxel size it solves."""
+    nmax = ctypes.c_int32()
+    rc = lib().gp_voxels_solve_alg3(h, _ptr(xyz), _ptr(offsets), int(nvox), _ptr(centres),
+                                    _ptr(lam), _ptr(sf2), _ptr(sn2), _ptr(axis), _ptr(mean),
+                                    _ptr(cov), _ptr(status), _stream(stream), ctypes.byref(nmax))
+    _check("gp_voxels_solve_alg3", rc)
+    return nmax.value
 
 
 def gp_voxels_scan_types(h, slot, before=None, after=None, stream=None) -> None:
