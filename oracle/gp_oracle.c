@@ -466,6 +466,37 @@ done:
 }
 
 /* ------------------------------------------------------------------ */
+/* Structure similarity loss of Eq. 11: for every scan point P_j, the  */
+/* minimum over all Gaussians k of |P_j - p_k| - mean(S_k), and the    */
+/* mean of those minima over the points.  Brute force over k (ties:    */
+/* the smallest k).  best[j], arg[j] per point; returns the mean.      */
+/* ------------------------------------------------------------------ */
+double gpo_structure_loss(const float* pts, int64_t n, const float* gpos, const float* gscale,
+                          int64_t m, double* best, int64_t* arg)
+{
+    double total = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double b = 0.0;
+        int64_t bk = -1;
+        for (int64_t k = 0; k < m; ++k) {
+            double dx = (double)pts[3 * j] - (double)gpos[3 * k];
+            double dy = (double)pts[3 * j + 1] - (double)gpos[3 * k + 1];
+            double dz = (double)pts[3 * j + 2] - (double)gpos[3 * k + 2];
+            double sbar = ((double)gscale[3 * k] + (double)gscale[3 * k + 1] + (double)gscale[3 * k + 2]) / 3.0;
+            double v = sqrt(dx * dx + dy * dy + dz * dz) - sbar;
+            if (bk < 0 || v < b) {
+                b = v;
+                bk = k;
+            }
+        }
+        if (best) best[j] = b;
+        if (arg) arg[j] = bk;
+        total += b;
+    }
+    return n > 0 ? total / (double)n : 0.0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Quaternion (w, x, y, z) of a proper rotation matrix R (row-major), */
 /* the textbook trace/major-diagonal branches; sign fixed to w >= 0.  */
 /* ------------------------------------------------------------------ */

@@ -58,6 +58,8 @@ def lib():
         _lib.gpo_solve_voxel_fullcov.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_int, ctypes.c_int, P, P, P]
+        _lib.gpo_structure_loss.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int64, P, P]
+        _lib.gpo_structure_loss.restype = ctypes.c_double
         _lib.gpo_init_voxel.argtypes = [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, P, P, P, P]
@@ -150,6 +152,19 @@ def solve_voxel_fullcov(xyz, centre, size, G, lam, sf2, sn2, mean_mode=1, axis_o
                                        float(lam), float(sf2), float(sn2), int(mean_mode),
                                        int(axis_override), ctypes.byref(ax), _p(mean), _p(cov))
     return st, ax.value, mean, cov
+
+
+def structure_loss(points, gpos, gscale):
+    """Structure similarity loss of Eq. 11 by brute force: (L_p, best[n], arg[n]) with
+    best[j] = min_k |P_j - p_k| - mean(S_k) and arg[j] its k (ties: smallest k)."""
+    pts = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+    gp = np.ascontiguousarray(gpos, dtype=np.float32).reshape(-1, 3)
+    gs = np.ascontiguousarray(gscale, dtype=np.float32).reshape(-1, 3)
+    best = np.zeros(pts.shape[0])
+    arg = np.zeros(pts.shape[0], dtype=np.int64)
+    loss = lib().gpo_structure_loss(_p(pts), pts.shape[0], _p(gp), _p(gs), gp.shape[0],
+                                    _p(best), _p(arg))
+    return loss, best, arg
 
 
 def init_voxel(mean, var, axis, centre, size, G, n_s, n_r, sf2, init_mode=0):

@@ -246,16 +246,44 @@ __global__ void __launch_bounds__(kA3Threads) k_alg3_factor(Alg3Args a)
     const int Kp = a.kp;
     float* Pb = a.ws_pb + (int64_t)slot * Q * Kp;
     float* Ps = a.ws_ps + (int64_t)slot * Q * Kp;
-    for (int t = tid; t < Q * n; t += blockDim.x) {
-        const int q = t / n, c = t - q * n;
-        const int u = q / G, w = q - u * G;
-        const int sc = src[c];
-        float s = 0.f;
-        for (int j = 0; j < n; ++j) s = fmaf(fa[j * G + u] * fb[j * G + w], A[j * n + sc], s);
-        float bg, sl;
-        umma::tf32_split(s, bg, sl);
-        Pb[(int64_t)q * Kp + c] = bg;
-        Ps[(int64_t)q * Kp + c] = sl;
+    {  // 4 queries x 4 columns per thread, 16 accumulators
+        const int nqt = (Q + 3) >> 2, nct = (n + 3) >> 2;
+        for (int t = tid; t < nqt * nct; t += blockDim.x) {
+            const int qt = t / nct, ct = t - qt * nct;
+            int uq[4], wq[4], sc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int q = min(4 * qt + i, Q - 1), c = min(4 * ct + i, n - 1);
+                uq[i] = q / G;
+                wq[i] = q - uq[i] * G;
+                sc[i] = src[c];
+            }
+            float acc[4][4] = {};
+            for (int j = 0; j < n; ++j) {
+                float kq[4], x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    kq[i] = fa[j * G + uq[i]] * fb[j * G + wq[i]];
+                    x[i] = A[j * n + sc[i]];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(kq[i], x[k], acc[i][k]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int q = 4 * qt + i, c = 4 * ct + k;
+                    if (q < Q && c < n) {
+                        float bg, sl;
+                        umma::tf32_split(acc[i][k], bg, sl);
+                        Pb[(int64_t)q * Kp + c] = bg;
+                        Ps[(int64_t)q * Kp + c] = sl;
+                    }
+                }
+        }
     }
     // factors of K* for kernel B
     float* FA = a.ws_fa + (int64_t)slot * Kp * G;
