@@ -203,6 +203,29 @@ GPV_API int gp_voxels_solve_alg3(gp_voxels_t* h, const float* d_xyz, const int64
                                  float* d_mean, float* d_cov, uint32_t* d_status,
                                  gpv_stream_t stream, int32_t* h_nmax);
 
+/* Structure similarity loss of Eq. 11 (Sec. 3.3) between a set of 3D Gaussians and a
+ * scan: for every scan point P_j, best_j = min over the Gaussians k of
+ * |P_j - p_k| - mean(S_k) (the minimum of the expression as printed, which can pick a
+ * farther Gaussian with a larger scale than the nearest one), and L_p = mean_j best_j.
+ *   d_gpos [m, 3], d_gscale [m, 3]: Gaussian centres and scales (FP32, e.g. the d_pos
+ *       and d_scale outputs of a solve), m >= 1
+ *   d_points [n, 3]: the scan (FP32 world coordinates)
+ *   cell: side of the hash-grid cells the Gaussians are binned in (about their spacing,
+ *       e.g. voxel_size / n_s); any positive value gives the same result, only faster
+ *       or slower
+ * Outputs (device): d_best [n] FP32 and d_arg [n] int32 (the minimising k; ties: the
+ * smallest k), either may be NULL; d_loss [1] FP64 (mean over the points, fixed-order
+ * summation); d_info [2] int32 (optional): points settled by the exhaustive pass (no
+ * Gaussian within 16 cells), and 1 if the hash table overflowed (never with its sizing).
+ * The search is exact: cells are visited in growing rings until no farther Gaussian can
+ * beat the best value.  A call with more Gaussians or points than any earlier call of
+ * the handle grows its workspace (allocates, synchronises the device).
+ * Errors: GPV_EINVAL, GPV_EBUDGET, GPV_ENOMEM, GPV_ECUDA. */
+GPV_API int gp_voxels_structure_loss(gp_voxels_t* h, const float* d_gpos, const float* d_gscale,
+                                     int32_t m, const float* d_points, int32_t n, float cell,
+                                     float* d_best, int32_t* d_arg, double* d_loss,
+                                     int32_t* d_info, gpv_stream_t stream);
+
 /* Gaussian initialisation from given predictions (Sec. 3.2, Eq. 6-8): for each of the
  * n_s x n_s subgrids of each voxel, weights w = 1 / max(var, 1e-6 sf2), position
  * p = sum w P / sum w, Phi = sum w (P - p)(P - p)^T / sum w, then scale/rotation per

@@ -12,6 +12,7 @@
 #include "../../include/gp_voxels.h"
 #include "gpv_alg3.h"
 #include "gpv_internal.h"
+#include "gpv_lp.h"
 #include "gpv_store.h"
 
 using namespace gpv;
@@ -89,6 +90,17 @@ struct gp_voxels {
         uint32_t* st = nullptr;
         int32_t* n = nullptr;
     } a3;
+    // workspace of the structure similarity loss (grown on demand)
+    struct LpWork {
+        int32_t mcap = 0, ncap = 0;
+        uint32_t H = 0;
+        uint64_t* keys = nullptr;
+        int32_t *head = nullptr, *next = nullptr, *pending = nullptr, *counters = nullptr;
+        int32_t* arg = nullptr;
+        float* best = nullptr;
+        uint32_t* smax = nullptr;
+        double* partial = nullptr;
+    } lp;
 };
 
 static int prec_kind(int precision)
@@ -248,6 +260,9 @@ static void release(gp_voxels_t* h)
     cudaFree(h->d_one); cudaFree(h->d_ident); cudaFree(h->d_pl_next);
     cudaFree(h->a3.pb); cudaFree(h->a3.ps); cudaFree(h->a3.fa); cudaFree(h->a3.fb);
     cudaFree(h->a3.st); cudaFree(h->a3.n);
+    cudaFree(h->lp.keys); cudaFree(h->lp.head); cudaFree(h->lp.next); cudaFree(h->lp.pending);
+    cudaFree(h->lp.counters); cudaFree(h->lp.arg); cudaFree(h->lp.best); cudaFree(h->lp.smax);
+    cudaFree(h->lp.partial);
     store_destroy(h->store);
     delete h;
 }
@@ -594,6 +609,73 @@ extern "C" int gp_voxels_solve_alg3(gp_voxels_t* h, const float* d_xyz, const in
         CK(alg3_launch_chunk(a, std::min(h->a3.chunk, nvox - v0), (cudaStream_t)stream, &nl));
         h->last_launches += nl;
     }
+    return GPV_OK;
+}
+
+static constexpr int kLpPartial = 1024;
+
+// (Re)allocate the loss workspace for m Gaussians and n points.
+static int lp_workspace(gp_voxels_t* h, int32_t m, int32_t n)
+{
+    auto& w = h->lp;
+    if (m <= w.mcap && n <= w.ncap && w.keys) return GPV_OK;
+    const int32_t mc = std::max(m, w.mcap), nc = std::max(n, w.ncap);
+    uint32_t H = 1024;
+    while (H < 2u * (uint32_t)std::max(mc, 1)) H <<= 1;
+    cudaDeviceSynchronize();
+    cudaFree(w.keys); cudaFree(w.head); cudaFree(w.next); cudaFree(w.pending);
+    cudaFree(w.counters); cudaFree(w.arg); cudaFree(w.best); cudaFree(w.smax); cudaFree(w.partial);
+    w = gp_voxels::LpWork();
+    const size_t need = (size_t)H * 12 + (size_t)mc * 4 + (size_t)nc * 12 + 64 + kLpPartial * 8;
+    if (h->cfg.mem_budget && h->bytes + need > h->cfg.mem_budget) return GPV_EBUDGET;
+    auto al = [&](void** p, size_t b) -> int {
+        cudaError_t e = cudaMalloc(p, b);
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return GPV_ENOMEM; }
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->bytes += b;
+        return GPV_OK;
+    };
+    int rc;
+    if ((rc = al((void**)&w.keys, (size_t)H * 8)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.head, (size_t)H * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.next, (size_t)std::max(mc, 1) * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.pending, (size_t)std::max(nc, 1) * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.arg, (size_t)std::max(nc, 1) * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.best, (size_t)std::max(nc, 1) * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.counters, 16)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.smax, 16)) != GPV_OK) return rc;
+    if ((rc = al((void**)&w.partial, kLpPartial * 8)) != GPV_OK) return rc;
+    w.mcap = mc;
+    w.ncap = nc;
+    w.H = H;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_structure_loss(gp_voxels_t* h, const float* d_gpos,
+                                        const float* d_gscale, int32_t m, const float* d_points,
+                                        int32_t n, float cell, float* d_best, int32_t* d_arg,
+                                        double* d_loss, int32_t* d_info, gpv_stream_t stream)
+{
+    if (!h || m < 1 || n < 0 || !(cell > 0.f) || !d_gpos || !d_gscale || !d_loss) return GPV_EINVAL;
+    if (n > 0 && !d_points) return GPV_EINVAL;
+    int rc = lp_workspace(h, m, n);
+    if (rc != GPV_OK) return rc;
+    auto& w = h->lp;
+    LpArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = d_points; a.n = n; a.gpos = d_gpos; a.gscale = d_gscale; a.m = m; a.h = cell;
+    a.H = w.H; a.keys = w.keys; a.head = w.head; a.next = w.next; a.pending = w.pending;
+    a.counters = w.counters; a.smax = w.smax; a.partial = w.partial;
+    a.nb_partial = std::max(1, std::min(kLpPartial, (n + 255) / 256));
+    a.sms = h->sms;
+    a.best = d_best ? d_best : w.best;
+    a.arg = d_arg ? d_arg : w.arg;
+    a.loss = d_loss;
+    cudaStream_t s = (cudaStream_t)stream;
+    int nl = 0;
+    CK(lp_launch(a, s, &nl));
+    if (d_info) CK(cudaMemcpyAsync(d_info, w.counters, 8, cudaMemcpyDeviceToDevice, s));
+    h->last_launches = nl;
     return GPV_OK;
 }
 

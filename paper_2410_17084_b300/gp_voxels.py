@@ -29,6 +29,7 @@ EXPORTED = [
     "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
     "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
     "gp_voxels_scan_types", "gp_voxels_type_counts", "gp_voxels_solve_alg3",
+    "gp_voxels_structure_loss",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -109,6 +110,8 @@ def lib() -> ctypes.CDLL:
         L.gp_voxels_type_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
         L.gp_voxels_solve_alg3.argtypes = [P, P, P, ctypes.c_int32] + [P] * 9 + [
             ctypes.POINTER(ctypes.c_int32)]
+        L.gp_voxels_structure_loss.argtypes = [P, P, P, ctypes.c_int32, P, ctypes.c_int32,
+                                               ctypes.c_float, P, P, P, P, P]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -201,6 +204,16 @@ def gp_voxels_solve_alg3(h, xyz, offsets, nvox, centres, lam, sf2, sn2, axis, me
                                     _ptr(cov), _ptr(status), _stream(stream), ctypes.byref(nmax))
     _check("gp_voxels_solve_alg3", rc)
     return nmax.value
+
+
+def gp_voxels_structure_loss(h, gpos, gscale, m, points, n, cell, loss, best=None, arg=None,
+                             info=None, stream=None) -> None:
+    """Structure similarity loss of Eq. 11 into the device FP64 scalar ``loss``; per-point
+    minima and arguments into ``best`` / ``arg`` when given."""
+    rc = lib().gp_voxels_structure_loss(h, _ptr(gpos), _ptr(gscale), int(m), _ptr(points),
+                                        int(n), float(cell), _ptr(best), _ptr(arg), _ptr(loss),
+                                        _ptr(info), _stream(stream))
+    _check("gp_voxels_structure_loss", rc)
 
 
 def gp_voxels_scan_types(h, slot, before=None, after=None, stream=None) -> None:
