@@ -497,6 +497,159 @@ double gpo_structure_loss(const float* pts, int64_t n, const float* gpos, const 
 }
 
 /* ------------------------------------------------------------------ */
+/* Alpha-blending rasterisation of 3D Gaussians (Sec. 3.3, Eq. 9): the */
+/* colour C, depth D and silhouette S images of one pinhole camera.    */
+/* Per Gaussian (FP64): t = Rc p + tc; culled when t_z <= near; 2D     */
+/* mean u = fx t_x / t_z + cx, v = fy t_y / t_z + cy; covariance       */
+/* Sigma = R diag(s^2) R^T (R from the unit quaternion), projected     */
+/* Sigma' = J Rc Sigma Rc^T J^T + 0.3 I with the perspective Jacobian J */
+/* at t (t_x / t_z, t_y / t_z clamped to 1.3 times the half field of   */
+/* view); radius r = ceil(3 sqrt(lambda_max(Sigma'))).  A Gaussian     */
+/* reaches pixel (x, y) (centre x + 1/2, y + 1/2) when the centre lies */
+/* in [u - r, u + r] x [v - r, v + r]; there alpha = min(0.99, opacity */
+/* exp(-d^T Sigma'^-1 d / 2)), skipped below 1/255.  Front to back by  */
+/* depth t_z (ties: smaller index): C += c alpha T, D += t_z alpha T,  */
+/* S += alpha T, T *= 1 - alpha; blending stops before a Gaussian that */
+/* would take T below 1e-4.  amb[pixel] = 1 when a decision at that    */
+/* pixel (square membership, the 1/255 cut, the 1e-4 stop, the radius  */
+/* rounding) lies within 1e-4 (relative) of its threshold.             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double u, v, z, ca, cb, cc, r, op, col[3];
+    int ok, amb_r;
+} gpo_splat;
+
+typedef struct {
+    double z;
+    int64_t k;
+} gpo_zk;
+
+static int cmp_zk(const void* a, const void* b)
+{
+    const gpo_zk* x = (const gpo_zk*)a;
+    const gpo_zk* y = (const gpo_zk*)b;
+    if (x->z < y->z) return -1;
+    if (x->z > y->z) return 1;
+    return x->k < y->k ? -1 : (x->k > y->k ? 1 : 0);
+}
+
+void gpo_rasterize(const float* pos, const float* scale, const float* quat, const float* opac,
+                   const float* color, int64_t m, const double* Rc, const double* tc, double fx,
+                   double fy, double cx, double cy, int W, int H, double near, double* C,
+                   double* D, double* S, uint8_t* amb)
+{
+    gpo_splat* g = (gpo_splat*)malloc(sizeof(gpo_splat) * (size_t)(m > 0 ? m : 1));
+    const double limx = 1.3 * (double)W / (2.0 * fx), limy = 1.3 * (double)H / (2.0 * fy);
+    for (int64_t k = 0; k < m; ++k) {
+        gpo_splat* q = &g[k];
+        q->ok = 0;
+        q->amb_r = 0;
+        double t[3];
+        for (int a = 0; a < 3; ++a)
+            t[a] = Rc[3 * a] * pos[3 * k] + Rc[3 * a + 1] * pos[3 * k + 1] + Rc[3 * a + 2] * pos[3 * k + 2] + tc[a];
+        if (!(t[2] > near)) continue;
+        double qw = quat[4 * k], qx = quat[4 * k + 1], qy = quat[4 * k + 2], qz = quat[4 * k + 3];
+        double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+        double R[3][3] = {
+            {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+        double Sg[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int c = 0; c < 3; ++c) acc += R[a][c] * (double)scale[3 * k + c] * (double)scale[3 * k + c] * R[b][c];
+                Sg[a][b] = acc;
+            }
+        double xz = t[0] / t[2], yz = t[1] / t[2];
+        if (xz < -limx) xz = -limx;
+        if (xz > limx) xz = limx;
+        if (yz < -limy) yz = -limy;
+        if (yz > limy) yz = limy;
+        double J[2][3] = {{fx / t[2], 0.0, -fx * xz / t[2]}, {0.0, fy / t[2], -fy * yz / t[2]}};
+        double T2[2][3];  /* J Rc */
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int c = 0; c < 3; ++c) acc += J[a][c] * Rc[3 * c + b];
+                T2[a][b] = acc;
+            }
+        double P2[2][2];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                double acc = 0.0;
+                for (int c = 0; c < 3; ++c)
+                    for (int d = 0; d < 3; ++d) acc += T2[a][c] * Sg[c][d] * T2[b][d];
+                P2[a][b] = acc;
+            }
+        double sa = P2[0][0] + 0.3, sb = P2[0][1], sc = P2[1][1] + 0.3;
+        double det = sa * sc - sb * sb;
+        if (!(det > 0.0)) continue;
+        double mid = 0.5 * (sa + sc);
+        double disc = mid * mid - det;
+        double lmax = mid + sqrt(disc > 0.1 ? disc : 0.1);
+        double r3 = 3.0 * sqrt(lmax);
+        q->r = ceil(r3);
+        q->amb_r = fabs(r3 - floor(r3 + 0.5)) < 1e-4 * r3;
+        q->ca = sc / det;
+        q->cb = -sb / det;
+        q->cc = sa / det;
+        q->u = fx * t[0] / t[2] + cx;
+        q->v = fy * t[1] / t[2] + cy;
+        q->z = t[2];
+        q->op = opac[k];
+        for (int a = 0; a < 3; ++a) q->col[a] = color[3 * k + a];
+        q->ok = 1;
+    }
+    gpo_zk* list = (gpo_zk*)malloc(sizeof(gpo_zk) * (size_t)(m > 0 ? m : 1));
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const double px = x + 0.5, py = y + 0.5;
+            const int64_t o = (int64_t)y * W + x;
+            int a_flag = 0;
+            int64_t cnt = 0;
+            for (int64_t k = 0; k < m; ++k) {
+                const gpo_splat* q = &g[k];
+                if (!q->ok) continue;
+                const double ex = fabs(px - q->u), ey = fabs(py - q->v);
+                const double e = ex > ey ? ex : ey;
+                if (fabs(e - q->r) < 1e-4 * (q->r + 1.0) || (q->amb_r && fabs(e - q->r) < 1.5))
+                    a_flag = 1;
+                if (e > q->r) continue;
+                list[cnt].z = q->z;
+                list[cnt].k = k;
+                ++cnt;
+            }
+            qsort(list, (size_t)cnt, sizeof(gpo_zk), cmp_zk);
+            double T = 1.0, c3[3] = {0, 0, 0}, dd = 0.0, ss = 0.0;
+            for (int64_t i = 0; i < cnt; ++i) {
+                const gpo_splat* q = &g[list[i].k];
+                const double dx = px - q->u, dy = py - q->v;
+                const double power = -0.5 * (q->ca * dx * dx + q->cc * dy * dy) - q->cb * dx * dy;
+                if (power > 0.0) continue;
+                double alpha = q->op * exp(power);
+                if (alpha > 0.99) alpha = 0.99;
+                if (fabs(alpha - 1.0 / 255.0) < 1e-4 / 255.0) a_flag = 1;
+                if (alpha < 1.0 / 255.0) continue;
+                const double nt = T * (1.0 - alpha);
+                if (fabs(nt - 1e-4) < 1e-8) a_flag = 1;
+                if (nt < 1e-4) break;
+                for (int a = 0; a < 3; ++a) c3[a] += q->col[a] * alpha * T;
+                dd += q->z * alpha * T;
+                ss += alpha * T;
+                T = nt;
+            }
+            for (int a = 0; a < 3; ++a) C[3 * o + a] = c3[a];
+            D[o] = dd;
+            S[o] = ss;
+            if (amb) amb[o] = (uint8_t)a_flag;
+        }
+    free(list);
+    free(g);
+}
+
+/* ------------------------------------------------------------------ */
 /* Quaternion (w, x, y, z) of a proper rotation matrix R (row-major), */
 /* the textbook trace/major-diagonal branches; sign fixed to w >= 0.  */
 /* ------------------------------------------------------------------ */

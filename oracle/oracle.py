@@ -60,6 +60,9 @@ def lib():
                                                  ctypes.c_int, ctypes.c_int, P, P, P]
         _lib.gpo_structure_loss.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int64, P, P]
         _lib.gpo_structure_loss.restype = ctypes.c_double
+        _lib.gpo_rasterize.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P, P, P]
         _lib.gpo_init_voxel.argtypes = [P, P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, P, P, P, P]
@@ -165,6 +168,25 @@ def structure_loss(points, gpos, gscale):
     loss = lib().gpo_structure_loss(_p(pts), pts.shape[0], _p(gp), _p(gs), gp.shape[0],
                                     _p(best), _p(arg))
     return loss, best, arg
+
+
+def rasterize(pos, scale, quat, opacity, color, Rc, tc, fx, fy, cx, cy, W, H, near=0.2):
+    """Colour, depth and silhouette images of Eq. 9 (front-to-back alpha blending of the
+    projected Gaussians; see gpo_rasterize): (C [H, W, 3], D [H, W], S [H, W], amb [H, W])
+    with amb marking pixels where a threshold decision is within rounding."""
+    f32 = lambda a, k: np.ascontiguousarray(a, dtype=np.float32).reshape(-1, k)
+    pos, scale, quat, color = f32(pos, 3), f32(scale, 3), f32(quat, 4), f32(color, 3)
+    opacity = np.ascontiguousarray(opacity, dtype=np.float32).reshape(-1)
+    Rc = np.ascontiguousarray(Rc, dtype=np.float64).reshape(3, 3)
+    tc = np.ascontiguousarray(tc, dtype=np.float64).reshape(3)
+    C = np.zeros((H, W, 3))
+    D = np.zeros((H, W))
+    S = np.zeros((H, W))
+    amb = np.zeros((H, W), dtype=np.uint8)
+    lib().gpo_rasterize(_p(pos), _p(scale), _p(quat), _p(opacity), _p(color), pos.shape[0],
+                        _p(Rc), _p(tc), float(fx), float(fy), float(cx), float(cy), int(W),
+                        int(H), float(near), _p(C), _p(D), _p(S), _p(amb))
+    return C, D, S, amb
 
 
 def init_voxel(mean, var, axis, centre, size, G, n_s, n_r, sf2, init_mode=0):
