@@ -627,7 +627,6 @@ void gpo_rasterize(const float* pos, const float* scale, const float* quat, cons
                 const gpo_splat* q = &g[list[i].k];
                 const double dx = px - q->u, dy = py - q->v;
                 const double power = -0.5 * (q->ca * dx * dx + q->cc * dy * dy) - q->cb * dx * dy;
-                if (power > 0.0) continue;
                 double alpha = q->op * exp(power);
                 if (alpha > 0.99) alpha = 0.99;
                 if (fabs(alpha - 1.0 / 255.0) < 1e-4 / 255.0) a_flag = 1;
