@@ -226,6 +226,37 @@ GPV_API int gp_voxels_structure_loss(gp_voxels_t* h, const float* d_gpos, const 
                                      float* d_best, int32_t* d_arg, double* d_loss,
                                      int32_t* d_info, gpv_stream_t stream);
 
+/* A pinhole camera for gp_voxels_render: camera coordinates t = R p + t_wc of a world
+ * point p (R row-major), image coordinates u = fx t_x / t_z + cx, v = fy t_y / t_z + cy in
+ * pixels (pixel (x, y) spans [x, x + 1) x [y, y + 1), its centre at x + 1/2, y + 1/2). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int width, height;
+    float near;  /* Gaussians with t_z <= near are not drawn */
+} gp_raster_camera;
+
+/* Rasterisation of 3D Gaussians into colour, depth and silhouette images (Sec. 3.3, Eq. 9,
+ * with depth and silhouette blended alike): every Gaussian with t_z > near is projected
+ * (covariance R diag(scale^2) R^T from the unit quaternion, Sigma' = J R_c Sigma R_c^T J^T
+ * + 0.3 I with the perspective Jacobian J, its t_x / t_z and t_y / t_z clamped to 1.3 times
+ * the half field of view) and reaches the pixels whose centres lie within
+ * r = ceil(3 sqrt(lambda_max(Sigma'))) of its projected centre along both image axes;
+ * there alpha = min(0.99, opacity exp(-d^T Sigma'^-1 d / 2)), ignored below 1/255.  In
+ * order of depth t_z (ties: lower index), front to back: C += color alpha T, D += t_z alpha
+ * T, S += alpha T, T *= 1 - alpha, stopping before a Gaussian that would take T below 1e-4.
+ *   d_pos, d_scale [m, 3], d_quat [m, 4] (w, x, y, z), d_opacity [m], d_color [m, 3]: FP32
+ *   outputs: d_image [H, W, 3], d_depth [H, W], d_silhouette [H, W] FP32 (every pixel written)
+ * Synchronises `stream` once (the size of the per-tile lists decides their buffer, which
+ * is grown when needed).  *h_pairs (may be NULL): (tile, Gaussian) pairs.
+ * Errors: GPV_EINVAL, GPV_ENOMEM, GPV_EFULL (more than 2^31 - 1 pairs), GPV_ECUDA. */
+GPV_API int gp_voxels_render(gp_voxels_t* h, const float* d_pos, const float* d_scale,
+                             const float* d_quat, const float* d_opacity, const float* d_color,
+                             int32_t m, const gp_raster_camera* cam, float* d_image,
+                             float* d_depth, float* d_silhouette, gpv_stream_t stream,
+                             int64_t* h_pairs);
+
 /* Gaussian initialisation from given predictions (Sec. 3.2, Eq. 6-8): for each of the
  * n_s x n_s subgrids of each voxel, weights w = 1 / max(var, 1e-6 sf2), position
  * p = sum w P / sum w, Phi = sum w (P - p)(P - p)^T / sum w, then scale/rotation per

@@ -508,14 +508,20 @@ double gpo_structure_loss(const float* pts, int64_t n, const float* gpos, const 
 /* reaches pixel (x, y) (centre x + 1/2, y + 1/2) when the centre lies */
 /* in [u - r, u + r] x [v - r, v + r]; there alpha = min(0.99, opacity */
 /* exp(-d^T Sigma'^-1 d / 2)), skipped below 1/255.  Front to back by  */
-/* depth t_z (ties: smaller index): C += c alpha T, D += t_z alpha T,  */
+/* depth (ties: smaller index): C += c alpha T, D += t_z alpha T,      */
 /* S += alpha T, T *= 1 - alpha; blending stops before a Gaussian that */
 /* would take T below 1e-4.  amb[pixel] = 1 when a decision at that    */
-/* pixel (square membership, the 1/255 cut, the 1e-4 stop, the radius  */
-/* rounding) lies within 1e-4 (relative) of its threshold.             */
+/* pixel lies within FP32 rounding of its threshold: bit 0 square      */
+/* membership (1e-6 of |u| + |v| + r), bit 1 the radius rounding (3     */
+/* sqrt(lambda_max) within 1e-5 of an integer, pixels within 1 of the  */
+/* edge), bit 2 the 1/255 cut and bit 3 the 1e-4 stop (1e-5 relative). */
+/* The depth that orders and culls is computed in FP32 as the kernel   */
+/* does (same operations, same order, each rounded), so those decisions */
+/* match exactly.                                                      */
 /* ------------------------------------------------------------------ */
 typedef struct {
     double u, v, z, ca, cb, cc, r, op, col[3];
+    float zkey;
     int ok, amb_r;
 } gpo_splat;
 
@@ -547,7 +553,12 @@ void gpo_rasterize(const float* pos, const float* scale, const float* quat, cons
         double t[3];
         for (int a = 0; a < 3; ++a)
             t[a] = Rc[3 * a] * pos[3 * k] + Rc[3 * a + 1] * pos[3 * k + 1] + Rc[3 * a + 2] * pos[3 * k + 2] + tc[a];
-        if (!(t[2] > near)) continue;
+        /* the depth that orders and culls: FP32, rounded after each operation in this
+           order, so the kernel takes the same decisions (its inputs are FP32) */
+        const float zk = (((float)Rc[6] * pos[3 * k]) + ((float)Rc[7] * pos[3 * k + 1])) +
+                         ((float)Rc[8] * pos[3 * k + 2]) + (float)tc[2];
+        q->zkey = zk;
+        if (!(zk > (float)near)) continue;
         double qw = quat[4 * k], qx = quat[4 * k + 1], qy = quat[4 * k + 2], qz = quat[4 * k + 3];
         double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
         qw /= qn; qx /= qn; qy /= qn; qz /= qn;
@@ -591,7 +602,7 @@ void gpo_rasterize(const float* pos, const float* scale, const float* quat, cons
         double lmax = mid + sqrt(disc > 0.1 ? disc : 0.1);
         double r3 = 3.0 * sqrt(lmax);
         q->r = ceil(r3);
-        q->amb_r = fabs(r3 - floor(r3 + 0.5)) < 1e-4 * r3;
+        q->amb_r = fabs(r3 - floor(r3 + 0.5)) < 1e-5 * r3;
         q->ca = sc / det;
         q->cb = -sb / det;
         q->cc = sa / det;
@@ -614,10 +625,17 @@ void gpo_rasterize(const float* pos, const float* scale, const float* quat, cons
                 if (!q->ok) continue;
                 const double ex = fabs(px - q->u), ey = fabs(py - q->v);
                 const double e = ex > ey ? ex : ey;
-                if (fabs(e - q->r) < 1e-4 * (q->r + 1.0) || (q->amb_r && fabs(e - q->r) < 1.5))
-                    a_flag = 1;
+                if (e <= q->r + 1.0 && e >= q->r - 1.0) {
+                    /* the square's edge matters only where the Gaussian would be drawn */
+                    const double dx = px - q->u, dy = py - q->v;
+                    const double pw = -0.5 * (q->ca * dx * dx + q->cc * dy * dy) - q->cb * dx * dy;
+                    if (q->op * exp(pw) >= (1.0 - 1e-5) / 255.0) {
+                        if (fabs(e - q->r) < 1e-6 * (fabs(q->u) + fabs(q->v) + q->r + 1.0)) a_flag |= 1;
+                        if (q->amb_r) a_flag |= 2;
+                    }
+                }
                 if (e > q->r) continue;
-                list[cnt].z = q->z;
+                list[cnt].z = (double)q->zkey;
                 list[cnt].k = k;
                 ++cnt;
             }
@@ -629,10 +647,10 @@ void gpo_rasterize(const float* pos, const float* scale, const float* quat, cons
                 const double power = -0.5 * (q->ca * dx * dx + q->cc * dy * dy) - q->cb * dx * dy;
                 double alpha = q->op * exp(power);
                 if (alpha > 0.99) alpha = 0.99;
-                if (fabs(alpha - 1.0 / 255.0) < 1e-4 / 255.0) a_flag = 1;
+                if (fabs(alpha - 1.0 / 255.0) < 1e-5 / 255.0) a_flag |= 4;
                 if (alpha < 1.0 / 255.0) continue;
                 const double nt = T * (1.0 - alpha);
-                if (fabs(nt - 1e-4) < 1e-8) a_flag = 1;
+                if (fabs(nt - 1e-4) < 1e-9) a_flag |= 8;
                 if (nt < 1e-4) break;
                 for (int a = 0; a < 3; ++a) c3[a] += q->col[a] * alpha * T;
                 dd += q->z * alpha * T;

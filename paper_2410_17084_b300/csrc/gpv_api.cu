@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <new>
 #include <vector>
 
@@ -13,6 +14,7 @@
 #include "gpv_alg3.h"
 #include "gpv_internal.h"
 #include "gpv_lp.h"
+#include "gpv_raster.h"
 #include "gpv_store.h"
 
 using namespace gpv;
@@ -101,6 +103,15 @@ struct gp_voxels {
         uint32_t* smax = nullptr;
         double* partial = nullptr;
     } lp;
+    // workspace of the rasteriser (grown on demand)
+    struct RsWork {
+        int32_t mcap = 0, tcap = 0;
+        int64_t kcap = 0;
+        float4* sp = nullptr;
+        int4* rect = nullptr;
+        int32_t *count = nullptr, *off = nullptr, *cursor = nullptr;
+        uint64_t* keys = nullptr;
+    } rs;
 };
 
 static int prec_kind(int precision)
@@ -263,6 +274,8 @@ static void release(gp_voxels_t* h)
     cudaFree(h->lp.keys); cudaFree(h->lp.head); cudaFree(h->lp.next); cudaFree(h->lp.pending);
     cudaFree(h->lp.counters); cudaFree(h->lp.arg); cudaFree(h->lp.best); cudaFree(h->lp.smax);
     cudaFree(h->lp.partial);
+    cudaFree(h->rs.sp); cudaFree(h->rs.rect); cudaFree(h->rs.count); cudaFree(h->rs.off);
+    cudaFree(h->rs.cursor); cudaFree(h->rs.keys);
     store_destroy(h->store);
     delete h;
 }
@@ -676,6 +689,76 @@ extern "C" int gp_voxels_structure_loss(gp_voxels_t* h, const float* d_gpos,
     CK(lp_launch(a, s, &nl));
     if (d_info) CK(cudaMemcpyAsync(d_info, w.counters, 8, cudaMemcpyDeviceToDevice, s));
     h->last_launches = nl;
+    return GPV_OK;
+}
+
+static int dev_alloc(gp_voxels_t* h, void** p, size_t b)
+{
+    cudaError_t e = cudaMalloc(p, b);
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return GPV_ENOMEM; }
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->bytes += b;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_render(gp_voxels_t* h, const float* d_pos, const float* d_scale,
+                                const float* d_quat, const float* d_opacity,
+                                const float* d_color, int32_t m, const gp_raster_camera* cam,
+                                float* d_image, float* d_depth, float* d_silhouette,
+                                gpv_stream_t stream, int64_t* h_pairs)
+{
+    if (!h || !cam || m < 0 || !d_image || !d_depth || !d_silhouette) return GPV_EINVAL;
+    if (m > 0 && (!d_pos || !d_scale || !d_quat || !d_opacity || !d_color)) return GPV_EINVAL;
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384 ||
+        !(cam->fx > 0.f) || !(cam->fy > 0.f) || !(cam->near > 0.f))
+        return GPV_EINVAL;
+    auto& w = h->rs;
+    const int tx = (cam->width + 15) / 16, ty = (cam->height + 15) / 16, nt = tx * ty;
+    int rc;
+    if (m > w.mcap || nt > w.tcap || !w.count) {
+        cudaDeviceSynchronize();
+        const int32_t mc = std::max(m, w.mcap), tc = std::max(nt, w.tcap);
+        cudaFree(w.sp); cudaFree(w.rect); cudaFree(w.count); cudaFree(w.off); cudaFree(w.cursor);
+        w.sp = nullptr; w.rect = nullptr; w.count = w.off = w.cursor = nullptr;
+        w.mcap = w.tcap = 0;
+        if ((rc = dev_alloc(h, (void**)&w.sp, sizeof(float4) * 3 * (size_t)std::max(mc, 1))) != GPV_OK) return rc;
+        if ((rc = dev_alloc(h, (void**)&w.rect, sizeof(int4) * (size_t)std::max(mc, 1))) != GPV_OK) return rc;
+        if ((rc = dev_alloc(h, (void**)&w.count, sizeof(int32_t) * (size_t)tc)) != GPV_OK) return rc;
+        if ((rc = dev_alloc(h, (void**)&w.off, sizeof(int32_t) * (size_t)(tc + 1))) != GPV_OK) return rc;
+        if ((rc = dev_alloc(h, (void**)&w.cursor, sizeof(int32_t) * (size_t)tc)) != GPV_OK) return rc;
+        w.mcap = mc;
+        w.tcap = tc;
+    }
+    RasterArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pos = d_pos; a.scale = d_scale; a.quat = d_quat; a.opacity = d_opacity; a.color = d_color;
+    a.m = m;
+    memcpy(a.cam.R, cam->R, sizeof(a.cam.R));
+    memcpy(a.cam.t, cam->t, sizeof(a.cam.t));
+    a.cam.fx = cam->fx; a.cam.fy = cam->fy; a.cam.cx = cam->cx; a.cam.cy = cam->cy;
+    a.cam.width = cam->width; a.cam.height = cam->height; a.cam.near = cam->near;
+    a.tiles_x = tx; a.tiles_y = ty; a.ntile = nt;
+    a.sp = w.sp; a.rect = w.rect; a.tile_count = w.count; a.tile_off = w.off; a.tile_cursor = w.cursor;
+    a.C = d_image; a.D = d_depth; a.S = d_silhouette;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(raster_prepare(a, s));
+    int32_t total = 0;  // the list size decides the key buffer: one host read per image
+    CK(cudaMemcpyAsync(&total, w.off + nt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (total < 0) return GPV_EFULL;  // more than 2^31 - 1 (tile, Gaussian) pairs
+    if (total > w.kcap) {
+        cudaFree(w.keys);
+        w.keys = nullptr;
+        w.kcap = 0;
+        const int64_t kc = std::max<int64_t>((int64_t)total + total / 4, 1 << 16);
+        if ((rc = dev_alloc(h, (void**)&w.keys, sizeof(uint64_t) * (size_t)kc)) != GPV_OK) return rc;
+        w.kcap = kc;
+    }
+    a.keys = w.keys;
+    a.cap = (int32_t)std::min<int64_t>(w.kcap, INT32_MAX);
+    CK(raster_finish(a, s));
+    h->last_launches = (m > 0 ? 2 : 1) + 3 + (m > 0 ? 1 : 0);
+    if (h_pairs) *h_pairs = total;
     return GPV_OK;
 }
 

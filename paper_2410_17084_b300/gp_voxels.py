@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -29,7 +30,7 @@ EXPORTED = [
     "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
     "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
     "gp_voxels_scan_types", "gp_voxels_type_counts", "gp_voxels_solve_alg3",
-    "gp_voxels_structure_loss",
+    "gp_voxels_structure_loss", "gp_voxels_render",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -59,6 +60,25 @@ class gp_voxels_config(ctypes.Structure):
         ("eta", ctypes.c_float),
         ("noise_floor", ctypes.c_float),
     ]
+
+
+class gp_raster_camera(ctypes.Structure):
+    _fields_ = [
+        ("R", ctypes.c_float * 9),
+        ("t", ctypes.c_float * 3),
+        ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+        ("width", ctypes.c_int), ("height", ctypes.c_int),
+        ("near", ctypes.c_float),
+    ]
+
+
+def make_camera(R, t, fx, fy, cx, cy, width, height, near=0.2) -> gp_raster_camera:
+    c = gp_raster_camera()
+    c.R[:] = [float(x) for x in np.asarray(R, dtype=np.float32).reshape(9)]
+    c.t[:] = [float(x) for x in np.asarray(t, dtype=np.float32).reshape(3)]
+    c.fx, c.fy, c.cx, c.cy = float(fx), float(fy), float(cx), float(cy)
+    c.width, c.height, c.near = int(width), int(height), float(near)
+    return c
 
 
 class GpvError(RuntimeError):
@@ -112,6 +132,9 @@ def lib() -> ctypes.CDLL:
             ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_structure_loss.argtypes = [P, P, P, ctypes.c_int32, P, ctypes.c_int32,
                                                ctypes.c_float, P, P, P, P, P]
+        L.gp_voxels_render.argtypes = [P, P, P, P, P, P, ctypes.c_int32,
+                                       ctypes.POINTER(gp_raster_camera), P, P, P, P,
+                                       ctypes.POINTER(ctypes.c_int64)]
         L.gp_voxels_last_error.argtypes = []
         L.gp_voxels_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -214,6 +237,18 @@ def gp_voxels_structure_loss(h, gpos, gscale, m, points, n, cell, loss, best=Non
                                         int(n), float(cell), _ptr(best), _ptr(arg), _ptr(loss),
                                         _ptr(info), _stream(stream))
     _check("gp_voxels_structure_loss", rc)
+
+
+def gp_voxels_render(h, pos, scale, quat, opacity, color, m, cam, image, depth, silhouette,
+                     stream=None) -> int:
+    """Colour, depth and silhouette images of m Gaussians (Eq. 9); returns the number of
+    (tile, Gaussian) pairs."""
+    pairs = ctypes.c_int64()
+    rc = lib().gp_voxels_render(h, _ptr(pos), _ptr(scale), _ptr(quat), _ptr(opacity),
+                                _ptr(color), int(m), ctypes.byref(cam), _ptr(image), _ptr(depth),
+                                _ptr(silhouette), _stream(stream), ctypes.byref(pairs))
+    _check("gp_voxels_render", rc)
+    return pairs.value
 
 
 def gp_voxels_scan_types(h, slot, before=None, after=None, stream=None) -> None:
