@@ -111,6 +111,10 @@ typedef struct {
                             table) */
     float noise_floor;   /* lower bound of a point's fed-back noise variance (keeps the
                             Gram matrix conditioned); the paper gives none */
+    int factor_panel;    /* 0: default factor (per column for 8-byte voxels up to 96
+                            points, else blocked with 16-column panels); 4, 8 or 16: the
+                            blocked shared-memory Cholesky with that panel width for every
+                            voxel; gp_voxels_autotune may choose otherwise per size bucket */
 } gp_voxels_config;
 
 /* Voxel types of Sec. 3.3 (gp_voxels_scan_types, gp_voxels_type_counts). */
@@ -384,8 +388,8 @@ GPV_API int gp_voxels_query_sizes(const gp_voxels_config* cfg, size_t* bytes_out
 /* Autotuner of the batched solve (the paper has no counterpart; its batch is a library
  * call): runs every size bucket of this batch with each candidate CTA size (128, 256 and
  * 512 threads, at least the bucket's largest n for shared-memory factors) and factor
- * variant (blocked or per-column, shared-memory buckets), persistent grids sized by
- * occupancy, and keeps the fastest per bucket in the
+ * variant (blocked with 16-, 8- or 4-column panels, or per column; shared-memory buckets),
+ * persistent grids sized by occupancy, and keeps the fastest per bucket in the
  * handle for later solves of any batch.  Inputs and outputs as gp_voxels_solve_csr (the
  * outputs are overwritten with scratch results; the FP64 escalation is not run).
  * Synchronises `stream`.  *h_changed = buckets whose choice changed.

@@ -42,6 +42,7 @@ struct Bucket {
     int grid;      // persistent CTAs
     bool tri_smem; // factor in shared memory (else in the global workspace slice)
     bool percol;   // per-column (not blocked) factor and inverse
+    int panel;     // panel width of the blocked factor (4, 8, 16)
 };
 
 struct PrecPlan {
@@ -133,6 +134,8 @@ static int validate(const gp_voxels_config* c)
     if (c->precision < 0 || c->precision > 2) return GPV_EINVAL;
     if (c->init_mode < 0 || c->init_mode > 1) return GPV_EINVAL;
     if (!(c->esc_cond > 1.f)) return GPV_EINVAL;
+    if (c->factor_panel != 0 && c->factor_panel != 4 && c->factor_panel != 8 && c->factor_panel != 16)
+        return GPV_EINVAL;
     if (c->hash_capacity & (c->hash_capacity - 1)) return GPV_EINVAL;
     if (c->hash_capacity > 0) {
         if (c->scan_slots < 1 || c->scan_slots > 64) return GPV_EINVAL;
@@ -177,7 +180,9 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         B.tri_smem = B.hi <= P.nmax_smem;
         // the workspace variant lays out its slice for max_points, whatever the bucket
         B.nthr = solve_threads(B.hi, B.tri_smem);
-        B.percol = B.tri_smem && B.hi <= default_percol_max(tsize(kind));
+        // an explicit panel width selects the blocked factor for every shared-memory bucket
+        B.percol = c.factor_panel == 0 && B.tri_smem && B.hi <= default_percol_max(tsize(kind));
+        B.panel = c.factor_panel > 0 ? c.factor_panel : 16;
         const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
                                       tsize(kind), B.tri_smem, B.nthr);
         if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) return GPV_EINVAL;  // panels too thin
@@ -468,6 +473,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             const Bucket& B = P.b[b];
             a.nmax = B.tri_smem ? B.hi : c.max_points;
             a.percol_max = B.percol ? B.hi : 0;
+            a.panel = B.panel;
             CK(launch_solve(kind, B.tri_smem, B.nthr, a, 1, B.smem, s));
             ++h->last_launches;
         }
@@ -490,6 +496,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_next = x.d_next + b;
         a.nmax = B.tri_smem ? B.hi : c.max_points;
         a.percol_max = B.percol ? B.hi : 0;
+        a.panel = B.panel;
         CK(launch_solve(kind, B.tri_smem, B.nthr, a, B.grid, B.smem, ss));
         ++h->last_launches;
         used |= 1 << (si % kNumBuckets);
@@ -509,6 +516,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_next = x.d_next + P.nb;
         a.nmax = a.nmax_small_f64;
         a.percol_max = default_percol_max(8);
+        a.panel = 16;
         CK(launch_solve(PREC_F64, true, solve_threads(a.nmax, true), a, h->esc_grid_small,
                         h->esc_smem_small, s));
         ++h->last_launches;
@@ -938,10 +946,13 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
         float best_ms = 3.0e38f;
         int best = B.nthr, best_smem = B.smem, best_grid = B.grid;
         bool best_pc = B.percol;
-        for (int ci = 0; ci < 6; ++ci) {
+        int best_pw = B.panel;
+        for (int ci = 0; ci < 12; ++ci) {
             const int nt = cand[ci % 3];
-            const bool pc = ci >= 3;  // per-column variant: shared-memory buckets only
-            if (pc && !B.tri_smem) continue;
+            const int var = ci / 3;  // blocked with 16-, 8- or 4-column panels, or per column
+            const bool pc = var == 3;
+            const int pw = var == 0 ? 16 : (var == 1 ? 8 : 4);
+            if (var > 0 && !B.tri_smem) continue;  // variants of the shared-memory factor
             if (B.tri_smem && nt < B.hi) continue;  // the shared-memory variants need n <= CTA size
             if (!B.tri_smem && nt < 256) continue;
             const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
@@ -957,6 +968,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
             a.work_next = x.d_next + b;
             a.nmax = B.tri_smem ? B.hi : c.max_points;
             a.percol_max = pc ? B.hi : 0;
+            a.panel = pw;
             float ms = 3.0e38f;
             for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel
                 CK(cudaMemsetAsync(x.d_next + b, 0, sizeof(int32_t), s));
@@ -970,10 +982,12 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
             }
             if (ms < best_ms) {
                 best_ms = ms; best = nt; best_smem = sp.total; best_grid = grid; best_pc = pc;
+                best_pw = pw;
             }
         }
-        if (best != B.nthr || best_pc != B.percol) ++changed;
+        if (best != B.nthr || best_pc != B.percol || best_pw != B.panel) ++changed;
         B.percol = best_pc;
+        B.panel = best_pw;
         B.nthr = best;
         B.smem = best_smem;
         B.grid = best_grid;

@@ -65,6 +65,7 @@ struct SolveArgs {
     int max_points;      // voxels with more points are reported VOX_TOO_LARGE
     int nmax_small_f64;  // escalated voxels up to this n take the shared-memory FP64 pass
     int percol_max;      // shared-memory voxels up to this n use the per-column factor/inverse
+    int panel;           // panel width of the blocked factor: 4, 8 or 16
 };
 
 // Shared-memory plan of one CTA (bytes), identical on host and device.

@@ -157,6 +157,7 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
     a.esc_list = scr + kOffEsc; a.esc_count = scr + kOffEscCount;
     a.gws = nullptr; a.gws_stride = 0;
     a.max_points = maxp;
+    a.panel = c->factor_panel > 0 ? c->factor_panel : 16;
     a.nmax_small_f64 = std::min(nsm64, maxp);
 
     k_set_bounds<<<1, 32, 0, s>>>(bnd, nb, scr + kOffHi);

@@ -133,6 +133,17 @@ __device__ __forceinline__ ff gsqrt(ff x)
     return fast_two_sum(s, r.hi * (0.5f * __frcp_rn(s)));
 }
 
+// 1 / sqrt(x): the FP32 hardware estimate y, one Newton step y + y (1 - x y^2) / 2 with
+// x y^2 formed in float-float (the estimate's error, about 2^-22, squares away)
+__device__ __forceinline__ float grsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double grsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ ff grsqrt(ff x)
+{
+    const float y = rsqrtf(x.hi);
+    const ff e = ff_make(1.f, 0.f) - (x * y) * y;
+    return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), e.hi));
+}
+
 // ---- reciprocal ---------------------------------------------------------------------
 __device__ __forceinline__ float grcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double grcp(double x) { return 1.0 / x; }

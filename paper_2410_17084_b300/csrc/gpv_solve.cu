@@ -85,27 +85,32 @@ __device__ __forceinline__ void trail_update(T* L, int n, int p0, int pw, int p1
     }
 }
 
-// Right-looking Cholesky by panels of 16 columns, in place in the packed triangle:
-// (a) the 16 x 16 diagonal block is factored by warp 0 in registers (lane r holds row r,
-//     updates exchanged by shuffles); (b) the rows below the block solve against it, one
-//     row per thread; (c) the trailing triangle takes the rank-16 update in 4 x 4
-//     register tiles.  Three barriers per panel.  ild[k] receives 1 / L_kk.  Returns
+// Right-looking Cholesky by panels of PW (4, 8 or 16) columns, in place in the packed
+// triangle: (a) the PW x PW diagonal block is factored by warp 0 in registers (lane r holds
+// row r, updates exchanged by shuffles); (b) the rows below the block solve against it, one
+// row per thread; (c) the trailing triangle takes the rank-PW update in 4 x 4 (or 2 x 2)
+// register tiles.  Three barriers per panel; narrower panels shorten the serial (a) and (b)
+// at the price of more barriers.  ild[k] receives 1 / L_kk.  Returns
 //     false at a non-positive pivot; s_dm holds the running min / max pivot.
-template <class T>
+template <class T, int PW>
 __device__ bool chol_smem(T* L, int n, T* ild, float* s_dm, int* s_fail)
 {
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
-    for (int p0 = 0; p0 < n; p0 += 16) {
-        const int pw = min(16, n - p0);
+    for (int p0 = 0; p0 < n; p0 += PW) {
+        const int pw = min(PW, n - p0);
         if (wid == 0) {
-            T row[16];
+            // unscaled: step c subtracts a(r, c) a(r2, c) / d_cc from the rows below, so only
+            // the reciprocal of the pivot is on the dependent chain; the square-root scaling
+            // of every column follows in one independent pass
+            T row[PW];
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < PW; ++c)
                 row[c] = (lane < pw && c <= lane) ? L[tri_off(p0 + c, n) + (lane - c)] : zero<T>();
             bool bad = false;
             float dmn = s_dm[0], dmx = s_dm[1];
+            T dg = zero<T>();  // lane c: the pivot d_cc
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < PW; ++c) {
                 if (c < pw && !bad) {  // warp-uniform
                     const T dcc = shfl_idx(row[c], c);
                     const float dh = hi_of(dcc);
@@ -114,27 +119,33 @@ __device__ bool chol_smem(T* L, int n, T* ild, float* s_dm, int* s_fail)
                     } else {
                         dmn = fminf(dmn, dh);
                         dmx = fmaxf(dmx, dh);
-                        const T lcc = gsqrt(dcc);
-                        const T il = grcp(lcc);
-                        if (lane == c) {
-                            row[c] = lcc;
-                            ild[p0 + c] = il;
-                        } else if (lane > c) {
-                            row[c] = row[c] * il;
-                        }
-                        const T lrc = row[c];
+                        if (lane == c) dg = dcc;
+                        const T ac = row[c];              // a(lane, c)
+                        const T tc = ac * grcp(dcc);      // a(lane, c) / d_cc
 #pragma unroll
-                        for (int r2 = c + 1; r2 < 16; ++r2) {
-                            const T v = shfl_idx(lrc, r2);  // l(r2, c)
-                            if (lane >= r2) row[r2] = gfnma(lrc, v, row[r2]);
+                        for (int r2 = c + 1; r2 < PW; ++r2) {
+                            const T v = shfl_idx(ac, r2);  // a(r2, c)
+                            if (lane >= r2) row[r2] = gfnma(tc, v, row[r2]);
                         }
                     }
                 }
             }
-            if (!bad && lane < pw)
+            if (!bad) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c <= lane) L[tri_off(p0 + c, n) + (lane - c)] = row[c];
+                for (int c = 0; c < PW; ++c) {
+                    const T rs = grsqrt(shfl_idx(dg, c));  // 1 / L_cc
+                    if (lane == c) {
+                        row[c] = dg * rs;                    // L_cc = d_cc / sqrt(d_cc)
+                        if (c < pw) ild[p0 + c] = rs;
+                    } else if (lane > c) {
+                        row[c] = row[c] * rs;
+                    }
+                }
+                if (lane < pw)
+#pragma unroll
+                    for (int c = 0; c < PW; ++c)
+                        if (c <= lane) L[tri_off(p0 + c, n) + (lane - c)] = row[c];
+            }
             if (lane == 0) {
                 s_dm[0] = dmn;
                 s_dm[1] = dmx;
@@ -145,21 +156,21 @@ __device__ bool chol_smem(T* L, int n, T* ild, float* s_dm, int* s_fail)
         if (*s_fail) return false;
         const int p1 = p0 + pw;
         for (int i = p1 + tid; i < n; i += nthr) {  // (b) panel rows below the block
-            T a[16];
+            T a[PW];
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < PW; ++c)
                 a[c] = c < pw ? L[tri_off(p0 + c, n) + (i - p0 - c)] : zero<T>();
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < PW; ++c) {
                 if (c < pw) {
                     a[c] = a[c] * ild[p0 + c];
 #pragma unroll
-                    for (int c2 = c + 1; c2 < 16; ++c2)
+                    for (int c2 = c + 1; c2 < PW; ++c2)
                         if (c2 < pw) a[c2] = gfnma(a[c], L[tri_off(p0 + c, n) + (c2 - c)], a[c2]);
                 }
             }
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < PW; ++c)
                 if (c < pw) L[tri_off(p0 + c, n) + (i - p0 - c)] = a[c];
         }
         __syncthreads();
@@ -177,19 +188,50 @@ __device__ bool chol_smem(T* L, int n, T* ild, float* s_dm, int* s_fail)
     return true;
 }
 
-// X = L^-1 in place by row blocks of 16 (rows above the block hold X, rows from the
-// block down hold L): (1) Y(r, c) = sum_{k=c}^{r0-1} L(r0+r, k) X(k, c) for c < r0, four
-// rows per task so the X(k, c) loads are shared; (2) Y is parked in the block's rows;
-// (3) one thread per column solves with the 16 x 16 diagonal block (X_II = L_II^-1 from
-// the identity); (4) results written back.  Four barriers per 16 rows.  Needs
-// n <= blockDim.x; ild[k] = 1 / L_kk from the factorisation.
+// X = L^-1 in place by row blocks of 16.  First every 16 x 16 diagonal block is inverted
+// in place, all blocks at once (thread per block column, forward substitution): these are
+// the diagonal blocks D of X.  Then, block row by block row (rows above hold X, rows from
+// the block down still hold L): (1) Y(r, c) = sum_{k=c}^{r0-1} L(r0+r, k) X(k, c) for
+// c < r0, four rows per task so the X(k, c) loads are shared, the lanes of a warp running
+// the k loop in step (their L loads are broadcasts); (2) Y parked in the block's rows;
+// (3) X(r0+r, c) = -sum_{q<=r} D(r, q) Y(q, c), again four rows per task; (4) written back.
+// Four barriers per block row, no dependent chain inside one.  Needs n <= blockDim.x.
 template <class T>
 __device__ void inv_smem(T* L, int n, const T* ild)
 {
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int r0 = 0; r0 < n; r0 += 16) {
+    const int nblk = (n + 15) >> 4;
+    {
+        const int b = tid >> 4, c = tid & 15, r0 = b << 4;
+        const int rb = min(16, n - r0);
+        const bool act = b < nblk && c < rb;
+        T z[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) z[r] = zero<T>();
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                if (r == c) {
+                    z[r] = ild[r0 + r];
+                } else if (r > c && r < rb) {
+                    T s2[2] = {zero<T>(), zero<T>()};
+#pragma unroll
+                    for (int q = 0; q < r; ++q)
+                        if (q >= c) acc_fma(s2[q & 1], L[tri_off(r0 + q, n) + (r - q)], z[q]);
+                    z[r] = -((acc_norm(s2[0]) + acc_norm(s2[1])) * ild[r0 + r]);
+                }
+            }
+        }
+        __syncthreads();
+        if (act)
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (r >= c && r < rb) L[tri_off(r0 + c, n) + (r - c)] = z[r];
+    }
+    for (int r0 = 16; r0 < n; r0 += 16) {
         const int rb = min(16, n - r0);
         const int ntask = 4 * r0;
+        __syncthreads();
         T y[4][4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -216,7 +258,7 @@ __device__ void inv_smem(T* L, int n, const T* ild)
         }
         __syncthreads();
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < 4; ++s) {  // park Y(r, c) in the block's rows
             const int t = tid + s * nthr;
             if (t < ntask) {
                 const int c = t % r0, g = t / r0;
@@ -228,37 +270,39 @@ __device__ void inv_smem(T* L, int n, const T* ild)
             }
         }
         __syncthreads();
-        const int c = tid;
-        const bool act = c < r0 + rb;
-        T z[16];
-        if (act) {
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                if (r < rb) {
-                    if (c < r0) z[r] = -L[tri_off(c, n) + (r0 + r - c)];
-                    else z[r] = from_f<T>(r0 + r == c ? 1.f : 0.f);
-                } else {
-                    z[r] = zero<T>();
-                }
-            }
+        for (int s = 0; s < 4; ++s) {  // X(r0 + r, c) = -sum_{q <= r} D(r, q) Y(q, c)
+            const int t = tid + s * nthr;
+            if (t < ntask) {
+                const int c = t % r0, g = t / r0;
+                const T* yc = L + tri_off(c, n) + (r0 - c);  // yc[q] = Y(q, c)
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                if (q < rb) {
-                    z[q] = z[q] * ild[r0 + q];
-                    const T* lq = L + tri_off(r0 + q, n) - (r0 + q) + r0;  // lq[r] = L(r0 + r, r0 + q)
+                for (int u = 0; u < 4; ++u) {
+                    const int r = g + 4 * u;
+                    T acc = zero<T>();
+                    if (r < rb)
 #pragma unroll
-                    for (int r = q + 1; r < 16; ++r)
-                        if (r < rb) z[r] = gfnma(lq[r], z[q], z[r]);
+                        for (int q = 0; q < 16; ++q)
+                            if (q <= r) acc_fma(acc, L[tri_off(r0 + q, n) + (r - q)], yc[q]);
+                    y[s][u] = -acc_norm(acc);
                 }
             }
         }
         __syncthreads();
-        if (act)
 #pragma unroll
-            for (int r = 0; r < 16; ++r)
-                if (r < rb && r0 + r >= c) L[tri_off(c, n) + (r0 + r - c)] = z[r];
-        __syncthreads();
+        for (int s = 0; s < 4; ++s) {
+            const int t = tid + s * nthr;
+            if (t < ntask) {
+                const int c = t % r0, g = t / r0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = g + 4 * u;
+                    if (r < rb) L[tri_off(c, n) + (r0 + r - c)] = y[s][u];
+                }
+            }
+        }
     }
+    __syncthreads();
 }
 
 // Per-column variants for small voxels in the 8-byte types, where one barrier per column
@@ -628,7 +672,9 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             __shared__ float s_dm[2];
             if (tid == 0) { s_dm[0] = 3.0e38f; s_dm[1] = 0.f; }
             __syncthreads();
-            chol_smem<T>(L, n, tmp, s_dm, &s_fail);
+            if (A.panel == 4) chol_smem<T, 4>(L, n, tmp, s_dm, &s_fail);
+            else if (A.panel == 8) chol_smem<T, 8>(L, n, tmp, s_dm, &s_fail);
+            else chol_smem<T, 16>(L, n, tmp, s_dm, &s_fail);
             dmin = s_dm[0];
             dmax = s_dm[1];
             __syncthreads();

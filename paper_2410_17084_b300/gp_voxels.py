@@ -59,6 +59,7 @@ class gp_voxels_config(ctypes.Structure):
         ("sn2", ctypes.c_float),
         ("eta", ctypes.c_float),
         ("noise_floor", ctypes.c_float),
+        ("factor_panel", ctypes.c_int),
     ]
 
 
