@@ -115,12 +115,14 @@ __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize
     if (!tri_in_smem) {
         const int work = kBigSmem - o;
         int pb = work > 0 ? work / (2 * nmax * tsize) : 0;
-        int rb = work > 0 ? work / (nmax * tsize) : 0;
+        // the inverse stages rb rows of the factor and a 16 x 16 block
+        int rb = work > 256 * tsize ? (work - 256 * tsize) / (nmax * tsize) : 0;
         pb = (pb > 32 ? 32 : pb) & ~3;
         rb = (rb > 16 ? 16 : rb) & ~3;
         p.pb = pb;
         p.rb = rb;
-        const int need = (2 * pb > rb ? 2 * pb : rb) * nmax * tsize;
+        const int need_f = 2 * pb * nmax * tsize, need_i = (rb * nmax + 256) * tsize;
+        const int need = need_f > need_i ? need_f : need_i;
         o = align16(o + need);
     }
     p.total = o;

@@ -489,54 +489,75 @@ __device__ bool big_cholesky(T* L, int n, T* P, T* Tt, int pb, float& dmin, floa
     return true;
 }
 
-// X = L^-1 in place by row blocks of rb rows (rows above the block already hold X, rows
-// from the block down still hold L): stage the block's rows of L, then for every column
-// c left of the block X_Ic = -L_II^-1 sum_k L_Ik X_kc (thread per column, rb
-// accumulators, rb <= 16), and X_II = L_II^-1; results go straight to global memory.
+// X = L^-1 in place by row blocks of rb (<= 16) rows (rows above the block already hold X,
+// rows from the block down still hold L): the block's rows of L are staged in shared
+// memory (W) and its diagonal block inverted there once (D, one warp, column by column);
+// then one warp per column c < r0 forms Y(r, c) = sum_{k=c}^{r0-1} L(r0+r, k) X(k, c), its
+// lanes striding over k so the reads of X's column are contiguous, reduces the 16 partial
+// sums across the warp, and lanes r < rb write X(r0+r, c) = -sum_{q<=r} D(r, q) Y(q, c);
+// the columns of the diagonal block take D itself.  W holds rb x n values, D 16 x 16.
 template <class T>
 __device__ void big_invert(T* L, int n, T* W, int rbmax)
 {
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    T* D = W + (int64_t)rbmax * n;  // 16 x 16, row-major
     for (int r0 = 0; r0 < n; r0 += rbmax) {
-        const int rb = min(rbmax, n - r0), cw = r0 + rb;
+        const int rb = min(rbmax, n - r0);
         __syncthreads();
-        for (int idx = tid; idx < rb * cw; idx += nthr) {
-            const int c = idx / rb, r = idx - c * rb;
+        for (int idx = tid; idx < rb * (r0 + rb); idx += nthr) {
+            const int r = idx / (r0 + rb), c = idx - r * (r0 + rb);
             if (c <= r0 + r) W[r * n + c] = L[tri_off(c, n) + (r0 + r - c)];
         }
         __syncthreads();
-        for (int c = tid; c < cw; c += nthr) {
+        if (wid == 0) {  // D = L_II^-1: lane c < rb solves column c
             T z[16];
 #pragma unroll
             for (int r = 0; r < 16; ++r) z[r] = zero<T>();
-            if (c < r0) {
-                const T* xc = L + tri_off(c, n);  // X[k][c] at xc[k - c], k < r0
-                for (int k = c; k < r0; ++k) {
-                    const T x = xc[k - c];
+            if (lane < rb) {
 #pragma unroll
-                    for (int r = 0; r < 16; ++r)
-                        if (r < rb) acc_fma(z[r], W[r * n + k], x);
+                for (int r = 0; r < 16; ++r) {
+                    if (r >= lane && r < rb) {
+                        T s2 = from_f<T>(r == lane ? 1.f : 0.f);
+#pragma unroll
+                        for (int q = 0; q < r; ++q)
+                            if (q >= lane) s2 = gfnma(W[r * n + r0 + q], z[q], s2);
+                        z[r] = s2 / W[r * n + r0 + r];
+                    }
                 }
 #pragma unroll
-                for (int r = 0; r < 16; ++r) z[r] = -acc_norm(z[r]);
-            } else {
+                for (int r = 0; r < 16; ++r) D[r * 16 + lane] = z[r];
+            }
+        }
+        __syncthreads();
+        for (int c = wid; c < r0 + rb; c += nw) {
+            if (c >= r0) {  // column of the diagonal block: X = D
+                if (lane < rb && lane >= c - r0)
+                    L[tri_off(c, n) + (r0 + lane - c)] = D[lane * 16 + (c - r0)];
+                continue;
+            }
+            T y[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) y[r] = zero<T>();
+            const T* xc = L + tri_off(c, n) - c;  // xc[k] = X(k, c), k >= c
+            for (int k = c + lane; k < r0; k += 32) {
+                const T x = xc[k];
 #pragma unroll
                 for (int r = 0; r < 16; ++r)
-                    if (r0 + r == c) z[r] = from_f<T>(1.f);
+                    if (r < rb) acc_fma(y[r], W[r * n + k], x);
             }
-            // forward substitution with L_II
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
-                if (r < rb) {
-                    T s = z[r];
+                y[r] = acc_norm(y[r]);
 #pragma unroll
-                    for (int q = 0; q < r; ++q) s = gfnma(W[r * n + r0 + q], z[q], s);
-                    z[r] = s / W[r * n + r0 + r];
-                }
+                for (int o = 16; o > 0; o >>= 1) y[r] = y[r] + shfl_x(y[r], o);
             }
+            if (lane < rb) {
+                T acc = zero<T>();
 #pragma unroll
-            for (int r = 0; r < 16; ++r)
-                if (r < rb && r0 + r >= c) L[tri_off(c, n) + (r0 + r - c)] = z[r];
+                for (int q = 0; q < 16; ++q)
+                    if (q <= lane) acc_fma(acc, D[lane * 16 + q], y[q]);
+                L[tri_off(c, n) + (r0 + lane - c)] = -acc_norm(acc);
+            }
         }
     }
     __syncthreads();
@@ -808,7 +829,22 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
 #pragma unroll
                     for (int r = 0; r < kQryBlk; ++r) acc[a][r] = zero<T>();
                 const int iend = min(j0 + kRowBlk, n);
-                for (int i = 0; i < iend; ++i) {
+                // columns left of the block: every row of a full block is below the diagonal
+                const int ifull = nrow == kRowBlk ? j0 : 0;
+                for (int i = 0; i < ifull; ++i) {
+                    const T ai = fa[i * G + u];
+                    T kq[kQryBlk];
+#pragma unroll
+                    for (int r = 0; r < kQryBlk; ++r) kq[r] = ai * fb[i * Gp + v0 + r];
+                    const T* col = L + tri_off(i, n) + (j0 - i);
+#pragma unroll
+                    for (int a = 0; a < kRowBlk; ++a) {
+                        const T l = col[a];
+#pragma unroll
+                        for (int r = 0; r < kQryBlk; ++r) acc_fma(acc[a][r], l, kq[r]);
+                    }
+                }
+                for (int i = ifull; i < iend; ++i) {
                     const T ai = fa[i * G + u];
                     T kq[kQryBlk];
 #pragma unroll
