@@ -442,25 +442,28 @@ __device__ bool big_cholesky(T* L, int n, T* P, T* Tt, int pb, float& dmin, floa
                 Tt[idx] = L[tri_off(k0 + kk, n) + (p0 - k0 - kk) + r];
             }
             __syncthreads();
-            for (int r = tid; r < R; r += nthr) {
-                for (int cg = 0; cg < pw; cg += 8) {
-                    T acc[8];
+            const int ncg = (pw + 7) >> 3;  // one task per (row, group of 8 panel columns)
+            for (int t = tid; t < R * ncg; t += nthr) {
+                const int r = t / ncg, cg = (t - r * ncg) * 8;
+                T acc[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[j] = zero<T>();
-                    for (int kk = 0; kk < kw; ++kk) {
-                        const T a = Tt[kk * R + r];
+                for (int j = 0; j < 8; ++j) acc[j] = zero<T>();
+                for (int kk = 0; kk < kw; ++kk) {
+                    const T a = Tt[kk * R + r];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (cg + j < pw) acc_fma(acc[j], a, Tt[kk * R + cg + j]);
-                    }
+                    for (int j = 0; j < 8; ++j)
+                        if (cg + j < pw) acc_fma(acc[j], a, Tt[kk * R + cg + j]);
+                }
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int c = cg + j;
-                        if (c < pw && r >= c) P[c * R + r] = P[c * R + r] - acc_norm(acc[j]);
-                    }
+                for (int j = 0; j < 8; ++j) {
+                    const int c = cg + j;
+                    if (c < pw && r >= c) P[c * R + r] = P[c * R + r] - acc_norm(acc[j]);
                 }
             }
         }
+        // the panel, right-looking and unscaled: step c subtracts P(r, c) P(c2, c) / d_c from
+        // the later columns and scales column c - 1 (not read by step c); one barrier per step
+        T rs_prev = zero<T>(), d_prev = zero<T>();
         for (int c = 0; c < pw; ++c) {
             __syncthreads();
             const T d = P[c * R + c];
@@ -468,17 +471,21 @@ __device__ bool big_cholesky(T* L, int n, T* P, T* Tt, int pb, float& dmin, floa
             if (!(dh > 0.f)) return false;
             dmin = fminf(dmin, dh);
             dmax = fmaxf(dmax, dh);
-            const T ld = gsqrt(d);
-            const T il = from_f<T>(1.f) / ld;
-            __syncthreads();
-            for (int r = c + tid; r < R; r += nthr) P[c * R + r] = (r == c) ? ld : P[c * R + r] * il;
-            __syncthreads();
+            const T inv_d = grcp(d);
+            if (c > 0)
+                for (int r = c - 1 + tid; r < R; r += nthr)
+                    P[(c - 1) * R + r] = (r == c - 1) ? d_prev * rs_prev : P[(c - 1) * R + r] * rs_prev;
             const int rest = pw - c - 1;
             for (int idx = tid; idx < rest * R; idx += nthr) {
                 const int c2 = c + 1 + idx / R, r = idx % R;
-                if (r >= c2) P[c2 * R + r] = gfnma(P[c * R + r], P[c * R + c2], P[c2 * R + r]);
+                if (r >= c2) P[c2 * R + r] = gfnma(P[c * R + r] * inv_d, P[c * R + c2], P[c2 * R + r]);
             }
+            d_prev = d;
+            rs_prev = grsqrt(d);
         }
+        __syncthreads();
+        for (int r = pw - 1 + tid; r < R; r += nthr)  // the last column's scaling
+            P[(pw - 1) * R + r] = (r == pw - 1) ? d_prev * rs_prev : P[(pw - 1) * R + r] * rs_prev;
         __syncthreads();
         for (int idx = tid; idx < pw * R; idx += nthr) {
             const int c = idx / R, r = idx - c * R;
