@@ -536,34 +536,46 @@ __device__ void big_invert(T* L, int n, T* W, int rbmax)
             }
         }
         __syncthreads();
-        for (int c = wid; c < r0 + rb; c += nw) {
-            if (c >= r0) {  // column of the diagonal block: X = D
-                if (lane < rb && lane >= c - r0)
-                    L[tri_off(c, n) + (r0 + lane - c)] = D[lane * 16 + (c - r0)];
-                continue;
-            }
+        // the columns of the diagonal block: X = D
+        for (int t = tid; t < rb * rb; t += nthr) {
+            const int cc = t / rb, r = t - cc * rb;
+            if (r >= cc) L[tri_off(r0 + cc, n) + (r - cc)] = D[r * 16 + cc];
+        }
+        // columns left of the block: 4 lanes per column, 8 columns per warp
+        const int sub = lane & 3;
+        for (int cb = wid * 8; cb < r0; cb += nw * 8) {
+            const int c = cb + (lane >> 2);
+            const bool act = c < r0;
             T y[16];
 #pragma unroll
             for (int r = 0; r < 16; ++r) y[r] = zero<T>();
-            const T* xc = L + tri_off(c, n) - c;  // xc[k] = X(k, c), k >= c
-            for (int k = c + lane; k < r0; k += 32) {
-                const T x = xc[k];
+            if (act) {
+                const T* xc = L + tri_off(c, n) - c;  // xc[k] = X(k, c), k >= c
+                for (int k = c + sub; k < r0; k += 4) {
+                    const T x = xc[k];
 #pragma unroll
-                for (int r = 0; r < 16; ++r)
-                    if (r < rb) acc_fma(y[r], W[r * n + k], x);
+                    for (int r = 0; r < 16; ++r)
+                        if (r < rb) acc_fma(y[r], W[r * n + k], x);
+                }
             }
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < 16; ++r) {  // sums over the column's 4 lanes
                 y[r] = acc_norm(y[r]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) y[r] = y[r] + shfl_x(y[r], o);
+                y[r] = y[r] + shfl_x(y[r], 1);
+                y[r] = y[r] + shfl_x(y[r], 2);
             }
-            if (lane < rb) {
-                T acc = zero<T>();
+            if (act) {  // lane sub writes rows sub, sub + 4, sub + 8, sub + 12
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (q <= lane) acc_fma(acc, D[lane * 16 + q], y[q]);
-                L[tri_off(c, n) + (r0 + lane - c)] = -acc_norm(acc);
+                for (int u = 0; u < 4; ++u) {
+                    const int r = sub + 4 * u;
+                    if (r < rb) {
+                        T acc = zero<T>();
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            if (q <= r) acc_fma(acc, D[r * 16 + q], y[q]);
+                        L[tri_off(c, n) + (r0 + r - c)] = -acc_norm(acc);
+                    }
+                }
             }
         }
     }
