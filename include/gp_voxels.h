@@ -405,6 +405,13 @@ GPV_API int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int64_t
  * handle queued (a diagnostic; the paper has no counterpart).  Errors: GPV_EINVAL. */
 GPV_API int gp_voxels_last_launches(const gp_voxels_t* h, int32_t* h_kernels);
 
+/* Arithmetic peak of this GPU measured with the solve's own arithmetic (the paper has no
+ * counterpart; a reference for roofline fractions): kind 0 = FP32 fused multiply-add, kind 1
+ * = the float-float accumulate-form multiply-add of the variance contraction; 2 flops per
+ * multiply-add, eight independent chains per thread on every SM, best of three launches.
+ * Synchronises `stream`.  Errors: GPV_EINVAL, GPV_ECUDA. */
+GPV_API int gp_voxels_measure_peak(int kind, gpv_stream_t stream, double* h_tflops);
+
 /* Static text of a gpv_status code. */
 GPV_API const char* gp_voxels_strerror(int status);
 

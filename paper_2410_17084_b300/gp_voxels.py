@@ -30,7 +30,7 @@ EXPORTED = [
     "gp_voxels_release_scan", "gp_voxels_store_voxels", "gp_voxels_solve_csr_noalloc",
     "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
     "gp_voxels_scan_types", "gp_voxels_type_counts", "gp_voxels_solve_alg3",
-    "gp_voxels_structure_loss", "gp_voxels_render",
+    "gp_voxels_structure_loss", "gp_voxels_render", "gp_voxels_measure_peak",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -133,6 +133,7 @@ def lib() -> ctypes.CDLL:
             ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_structure_loss.argtypes = [P, P, P, ctypes.c_int32, P, ctypes.c_int32,
                                                ctypes.c_float, P, P, P, P, P]
+        L.gp_voxels_measure_peak.argtypes = [I, P, ctypes.POINTER(ctypes.c_double)]
         L.gp_voxels_render.argtypes = [P, P, P, P, P, P, ctypes.c_int32,
                                        ctypes.POINTER(gp_raster_camera), P, P, P, P,
                                        ctypes.POINTER(ctypes.c_int64)]
@@ -250,6 +251,14 @@ def gp_voxels_render(h, pos, scale, quat, opacity, color, m, cam, image, depth, 
                                 _ptr(silhouette), _stream(stream), ctypes.byref(pairs))
     _check("gp_voxels_render", rc)
     return pairs.value
+
+
+def gp_voxels_measure_peak(kind: int, stream=None) -> float:
+    """Measured TFLOP/s: kind 0 FP32 FMA, kind 1 float-float accumulate-form FMA."""
+    t = ctypes.c_double()
+    _check("gp_voxels_measure_peak", lib().gp_voxels_measure_peak(int(kind), _stream(stream),
+                                                                  ctypes.byref(t)))
+    return t.value
 
 
 def gp_voxels_scan_types(h, slot, before=None, after=None, stream=None) -> None:
