@@ -405,6 +405,23 @@ def run_extras(b, d, stream, timed) -> dict:
             "GBps": ins_pts * 32 / (ins_ms * 1e-3) / 1e9,
             "bytes_per_point": "32 (12 point read + 12 bucket write + 8 key probe)",
             "ms_per_scan": ins_ms / nsc}
+        # the same scans with the voxel state machine of Sec. 3.3 (eta = 0.3, variance
+        # feedback): each insert waits for the previous scan's solve
+        fcfg = serve.serving_config(eta=0.3, noise_floor=4e-6)
+        srv4 = serve.Server(fcfg)
+        srv4.run(scans[:3], realtime=False)
+        srv4.close()
+        srv5 = serve.Server(fcfg)
+        flat, fwall, _ = srv5.run(scans, arrivals=scene.arrivals[:nsc], realtime=True)
+        types = gv.gp_voxels_type_counts(srv5.g.h)
+        srv5.close()
+        ex["serving_state_machine"] = {
+            "workload": f"the same {nsc} scans, voxel types (a)-(d) with eta = 0.3 and variance "
+                        "feedback (noise floor 4e-6)",
+            "p50_ms": float(np.percentile(flat * 1e3, 50)),
+            "p99_ms": float(np.percentile(flat * 1e3, 99)),
+            "max_ms": float(flat.max() * 1e3), "scans_per_s": nsc / fwall,
+            "voxel_types_abcd": types}
         ex["serving"] = {
             "workload": f"{nsc} synthetic 64x1024 LiDAR scans, Poisson arrivals at 10 Hz, "
                         "0.5 m voxels, 192-point buckets, G = 9, mixed precision + init",

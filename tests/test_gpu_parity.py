@@ -320,3 +320,14 @@ def test_factor_panel_widths(gpv, oracle, panel, precision):
     out = _run(gpv, b, precision, factor_panel=panel)
     tol = (MEAN_TOL, VAR_TOL) if precision else (FP32_MEAN_TOL, FP32_VAR_TOL)
     _check(gpv, b, out, oracle, *tol, f"panel {panel} prec={precision}")
+
+
+def test_measured_peaks_are_plausible(gpv):
+    """The arithmetic-peak probes: FP32 FMA rate below the unit-count bound (148 SMs x 128
+    lanes x 2 flops x 2.1 GHz) and the float-float multiply-add (12 FP32 operations) well
+    below the FP32 rate."""
+    fp32 = gpv.gp_voxels_measure_peak(0)
+    ffr = gpv.gp_voxels_measure_peak(1)
+    print(f"\nFP32 {fp32:.1f} TFLOP/s, float-float {ffr:.2f} TFLOP/s")
+    assert 10.0 < fp32 < 148 * 128 * 2 * 2.1e9 / 1e12
+    assert 0.5 < ffr < fp32 / 4
