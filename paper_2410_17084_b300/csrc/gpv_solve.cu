@@ -792,7 +792,12 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         tmp[j] = (acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3]));
     }
     // ---- A6: separable cross-covariance factors --------------------------------------
-    {
+    // On the uniform nodes u_k = u_0 + k delta, e_k = exp(-lambda (x - u_k)^2) obeys
+    // e_{k+1} = e_k r_k with r_k = exp(2 lambda delta (x - u_k) - lambda delta^2) and
+    // r_{k+1} = r_k exp(-2 lambda delta^2): three exponentials per point and axis (and one
+    // per voxel) instead of G, the rest products whose rounding grows only linearly in k
+    // (in the 8-byte types; FP32 evaluates every exponential, its variance has no margin)
+    if (sizeof(T) == 4) {
         for (int t0 = tid; t0 < n * G; t0 += 2 * nthr) {  // four exponentials in flight
             const int t1 = min(t0 + nthr, n * G - 1);
             const int i0 = t0 / G, u0 = t0 - i0 * G, i1 = t1 / G, u1 = t1 - i1 * G;
@@ -805,6 +810,33 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             if (t0 + nthr < n * G) {
                 fa[i1 * G + u1] = sf2 * ea1;
                 fb[i1 * Gp + u1] = eb1;
+            }
+        }
+        for (int t = tid; t < n * (Gp - G); t += nthr) {
+            const int i = t / (Gp - G), u = G + (t - i * (Gp - G));
+            fb[i * Gp + u] = zero<T>();
+        }
+    } else {
+        const T dl = from_d<T>((double)A.size / (double)G);
+        const T two = from_f<T>(2.f);
+        const T cst = gexp(nlam * (dl * dl) * two);  // exp(-2 lambda delta^2)
+        for (int t = tid; t < 2 * n; t += nthr) {
+            const int i = t >> 1;
+            const T d0 = ((t & 1) ? x2[i] : x1[i]) - nodes[0];  // x - u_0
+            T e = gexp(nlam * (d0 * d0));
+            T r = gexp(nlam * (dl * dl - two * dl * d0));
+            if ((t & 1) == 0) {
+                for (int k = 0; k < G; ++k) {
+                    fa[i * G + k] = sf2 * e;
+                    e = e * r;
+                    r = r * cst;
+                }
+            } else {
+                for (int k = 0; k < G; ++k) {
+                    fb[i * Gp + k] = e;
+                    e = e * r;
+                    r = r * cst;
+                }
             }
         }
         for (int t = tid; t < n * (Gp - G); t += nthr) {
