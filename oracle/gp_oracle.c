@@ -11,7 +11,7 @@
  * textbook loops, full n x n matrices, no blocking, no fusion, no reordering
  * beyond the definitions cited next to each function.
  *
- * Readings of the paper used here (each one is listed in the design doc):
+ * Readings of the paper used here, where it is silent or ambiguous:
  *   - kernel: k(a,b) = sf2 * exp(-lambda * |a-b|^2) (Sec. 3.1; the paper's
  *     setting is lambda = 1, sf2 = 1; a lengthscale l maps to 1/(2 l^2));
  *   - noise: sigma^2 = sn2 on the Gram diagonal (Eq. 2);

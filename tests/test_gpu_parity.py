@@ -5,8 +5,8 @@ Tolerances (stated once, used everywhere):
   mixed and FP64 paths: posterior mean max abs error <= 1e-4 m; variance relative error
   <= 1e-3 against max(var_ref, 1e-3 sigma^2); Gaussian init scale rel. error <= 1e-4 and
   rotation <= 1e-3 rad on pinned axes.
-  plain FP32 path: mean <= 1e-3 m and variance <= FP32_VAR_TOL (with
-  FP32 kernel values the variance moves by ~eps_32 |w|^2, beyond the 1e-3 target).
+  plain FP32 path: mean <= 1e-3 m and variance <= FP32_VAR_TOL (with FP32 kernel values
+  the variance moves by about eps_32 |w|^2, w the kriging weights, beyond the 1e-3 target).
 """
 import numpy as np
 import pytest
