@@ -412,6 +412,15 @@ GPV_API int gp_voxels_last_launches(const gp_voxels_t* h, int32_t* h_kernels);
  * Synchronises `stream`.  Errors: GPV_EINVAL, GPV_ECUDA. */
 GPV_API int gp_voxels_measure_peak(int kind, gpv_stream_t stream, double* h_tflops);
 
+/* Self-test of the bounded waits (no counterpart in the paper): every wait of this
+ * library's kernels on an mbarrier polls at most a fixed number of times, then reports
+ * (GPV_VOX_FAILED) and returns instead of hanging.  This call runs one such wait on an
+ * mbarrier that nothing arrives at, with `polls` tries (1 .. 2^24), and sets
+ * *h_timed_out = 1 when the wait gave up as it must.  Synchronises `stream`.
+ * Errors: GPV_EINVAL, GPV_ECUDA. */
+GPV_API int gp_voxels_selftest_bounded_wait(uint32_t polls, gpv_stream_t stream,
+                                            int32_t* h_timed_out);
+
 /* Static text of a gpv_status code. */
 GPV_API const char* gp_voxels_strerror(int status);
 

@@ -86,3 +86,47 @@ extern "C" int gp_voxels_measure_peak(int kind, gpv_stream_t stream, double* h_t
     *h_tflops = ops / (best * 1e-3) / 1e12;
     return GPV_OK;
 }
+
+namespace gpv {
+namespace {
+
+// One thread waits on an mbarrier that nothing arrives at, with the library's bounded
+// poll loop: the wait must give up after `polls` tries and say so.
+__global__ void k_bounded_wait(uint32_t polls, int32_t* timed_out)
+{
+    __shared__ __align__(8) uint64_t mbar;
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(1u) : "memory");
+    bool done = false;
+    for (uint32_t it = 0; it < polls && !done; ++it) {
+        uint32_t d;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(d) : "r"(a), "r"(0u) : "memory");
+        done = d != 0;
+    }
+    *timed_out = done ? 0 : 1;
+}
+
+}  // namespace
+}  // namespace gpv
+
+extern "C" int gp_voxels_selftest_bounded_wait(uint32_t polls, gpv_stream_t stream,
+                                               int32_t* h_timed_out)
+{
+    using namespace gpv;
+    if (!h_timed_out || polls == 0 || polls > (1u << 24)) return GPV_EINVAL;
+    int32_t* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int32_t));
+    if (e != cudaSuccess) { gpv_record_cuda_error(e); return GPV_ECUDA; }
+    cudaStream_t s = (cudaStream_t)stream;
+    k_bounded_wait<<<1, 1, 0, s>>>(polls, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_timed_out, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) { gpv_record_cuda_error(e); return GPV_ECUDA; }
+    return GPV_OK;
+}

@@ -31,6 +31,7 @@ EXPORTED = [
     "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
     "gp_voxels_scan_types", "gp_voxels_type_counts", "gp_voxels_solve_alg3",
     "gp_voxels_structure_loss", "gp_voxels_render", "gp_voxels_measure_peak",
+    "gp_voxels_selftest_bounded_wait",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -134,6 +135,7 @@ def lib() -> ctypes.CDLL:
         L.gp_voxels_structure_loss.argtypes = [P, P, P, ctypes.c_int32, P, ctypes.c_int32,
                                                ctypes.c_float, P, P, P, P, P]
         L.gp_voxels_measure_peak.argtypes = [I, P, ctypes.POINTER(ctypes.c_double)]
+        L.gp_voxels_selftest_bounded_wait.argtypes = [U32, P, ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_render.argtypes = [P, P, P, P, P, P, ctypes.c_int32,
                                        ctypes.POINTER(gp_raster_camera), P, P, P, P,
                                        ctypes.POINTER(ctypes.c_int64)]
@@ -259,6 +261,14 @@ def gp_voxels_measure_peak(kind: int, stream=None) -> float:
     _check("gp_voxels_measure_peak", lib().gp_voxels_measure_peak(int(kind), _stream(stream),
                                                                   ctypes.byref(t)))
     return t.value
+
+
+def gp_voxels_selftest_bounded_wait(polls: int, stream=None) -> bool:
+    """True when a bounded mbarrier wait that nothing completes gave up after ``polls``."""
+    t = ctypes.c_int32(-1)
+    _check("gp_voxels_selftest_bounded_wait",
+           lib().gp_voxels_selftest_bounded_wait(int(polls), _stream(stream), ctypes.byref(t)))
+    return t.value == 1
 
 
 def gp_voxels_scan_types(h, slot, before=None, after=None, stream=None) -> None:

@@ -331,3 +331,14 @@ def test_measured_peaks_are_plausible(gpv):
     print(f"\nFP32 {fp32:.1f} TFLOP/s, float-float {ffr:.2f} TFLOP/s")
     assert 10.0 < fp32 < 148 * 128 * 2 * 2.1e9 / 1e12
     assert 0.5 < ffr < fp32 / 4
+
+
+def test_bounded_wait_gives_up(gpv):
+    """A wait on an mbarrier that nothing completes ends after its poll limit and reports
+    it (the context stays usable: a solve runs afterwards)."""
+    assert gpv.gp_voxels_selftest_bounded_wait(1000)
+    assert gpv.gp_voxels_selftest_bounded_wait(1)
+    from paper_2410_17084_b300 import synth
+    b = synth.plane_batch(50, seed=9)
+    out = _run(gpv, b, 1)
+    assert ((out["status"].astype(np.uint32) & 0x15) == 0).all()
