@@ -115,6 +115,14 @@ typedef struct {
                             points, else blocked with 16-column panels); 4, 8 or 16: the
                             blocked shared-memory Cholesky with that panel width for every
                             voxel; gp_voxels_autotune may choose otherwise per size bucket */
+    int tc_workspace_mb; /* GPV_PREC_MIXED batch solves: MiB of device workspace for the
+                            posterior variance on the tensor cores (Eq. 3, diag(Sigma*) by
+                            exact BF16 slice products; voxels of up to 160 points whose factor
+                            fits shared memory).  A call whose eligible voxels need more than
+                            this forms every variance on the CUDA cores instead, so the
+                            choice never depends on scheduling.  0 turns it off; default
+                            4096; capped by what max_voxels voxels could use and, under
+                            mem_budget, by what the budget leaves. */
 } gp_voxels_config;
 
 /* Voxel types of Sec. 3.3 (gp_voxels_scan_types, gp_voxels_type_counts). */

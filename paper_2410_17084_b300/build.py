@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgp_voxels.so")
-SOURCES = ["gpv_api.cu", "gpv_solve.cu", "gpv_store.cu", "gpv_noalloc.cu", "gpv_alg3.cu", "gpv_lp.cu", "gpv_raster.cu", "gpv_peak.cu"]
+SOURCES = ["gpv_api.cu", "gpv_solve.cu", "gpv_store.cu", "gpv_noalloc.cu", "gpv_alg3.cu", "gpv_lp.cu", "gpv_raster.cu", "gpv_peak.cu", "gpv_vartc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -64,6 +64,12 @@ struct SolveCtx {
     int32_t* d_esc_list = nullptr;  // 2 * cap
     int32_t* d_esc_count = nullptr; // 2
     void* d_gws = nullptr;
+    // tensor-core variance (float-float): workspace, counters, queue (tc_cap 0 = off)
+    unsigned char* d_tc_ws = nullptr;
+    uint64_t tc_cap = 0;
+    TcCounters* d_tc = nullptr;
+    int32_t* d_tc_v = nullptr;
+    int64_t* d_tc_off = nullptr;
     cudaStream_t side[kNumBuckets] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kNumBuckets] = {};
@@ -134,6 +140,7 @@ static int validate(const gp_voxels_config* c)
     if (c->precision < 0 || c->precision > 2) return GPV_EINVAL;
     if (c->init_mode < 0 || c->init_mode > 1) return GPV_EINVAL;
     if (!(c->esc_cond > 1.f)) return GPV_EINVAL;
+    if (c->tc_workspace_mb < 0 || c->tc_workspace_mb > (1 << 20)) return GPV_EINVAL;
     if (c->factor_panel != 0 && c->factor_panel != 4 && c->factor_panel != 8 && c->factor_panel != 16)
         return GPV_EINVAL;
     if (c->hash_capacity & (c->hash_capacity - 1)) return GPV_EINVAL;
@@ -222,6 +229,7 @@ extern "C" int gp_voxels_config_default(gp_voxels_config* c)
     c->lambda = 1.f;
     c->sf2 = 1.f;
     c->sn2 = 4e-4f;
+    c->tc_workspace_mb = 4096;
     return GPV_OK;
 }
 
@@ -233,6 +241,20 @@ static size_t ctx_bytes(const gp_voxels_config* c, int cap, int sms, int Gp)
     return b;
 }
 
+// Workspace of the tensor-core variance of the batch entry: the configured size, no more
+// than max_voxels voxels of the largest eligible n could use, and (under a memory
+// budget) what the budget leaves; below 16 MB it is not worth keeping.
+static size_t tc_bytes(const gp_voxels_config* c, int Gp, size_t rest)
+{
+    if (c->precision != GPV_PREC_MIXED || c->tc_workspace_mb <= 0) return 0;
+    const int nmax = std::min(kTcMaxN, c->max_points);
+    size_t b = std::min((size_t)c->tc_workspace_mb << 20,
+                        (size_t)c->max_voxels * (size_t)tc_need_bytes(nmax, c->grid_side, Gp));
+    b += (size_t)c->max_voxels * (sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
+    if (c->mem_budget) b = c->mem_budget > rest ? std::min(b, c->mem_budget - rest) : 0;
+    return b < ((size_t)16 << 20) ? 0 : b;
+}
+
 static size_t solve_bytes(const gp_voxels_config* c, int sms, int Gp)
 {
     size_t b = ctx_bytes(c, c->max_voxels, sms, Gp);
@@ -242,13 +264,19 @@ static size_t solve_bytes(const gp_voxels_config* c, int sms, int Gp)
     return b;
 }
 
+static size_t solve_bytes_tc(const gp_voxels_config* c, int sms, int Gp)
+{
+    const size_t rest = solve_bytes(c, sms, Gp) + store_bytes(c);
+    return rest + tc_bytes(c, Gp, rest);
+}
+
 extern "C" int gp_voxels_query_sizes(const gp_voxels_config* c, size_t* bytes_out)
 {
     if (validate(c) != GPV_OK || !bytes_out) return GPV_EINVAL;
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int Gp = (c->grid_side + kQryBlk - 1) / kQryBlk * kQryBlk;
-    *bytes_out = solve_bytes(c, sms, Gp) + store_bytes(c);
+    *bytes_out = solve_bytes_tc(c, sms, Gp);
     return GPV_OK;
 }
 
@@ -256,6 +284,7 @@ static void ctx_release(SolveCtx& x)
 {
     cudaFree(x.d_bcount); cudaFree(x.d_bbase); cudaFree(x.d_bcursor); cudaFree(x.d_next);
     cudaFree(x.d_work); cudaFree(x.d_esc_list); cudaFree(x.d_esc_count); cudaFree(x.d_gws);
+    cudaFree(x.d_tc_ws); cudaFree(x.d_tc); cudaFree(x.d_tc_v); cudaFree(x.d_tc_off);
     for (int i = 0; i < kNumBuckets; ++i) {
         if (x.side[i]) cudaStreamDestroy(x.side[i]);
         if (x.ev_join[i]) cudaEventDestroy(x.ev_join[i]);
@@ -285,7 +314,7 @@ static void release(gp_voxels_t* h)
     delete h;
 }
 
-static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap)
+static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap, size_t tc_total = 0)
 {
     auto alloc = [&](void** p, size_t bytes) -> int {
         cudaError_t e = cudaMalloc(p, bytes);
@@ -305,6 +334,14 @@ static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap)
     AL(x.d_esc_list, sizeof(int32_t) * (size_t)cap * 2);
     AL(x.d_esc_count, sizeof(int32_t) * 2);
     AL(x.d_gws, 8 * (size_t)h->gws_stride * (size_t)h->gws_grid);
+    if (tc_total > 0) {
+        const size_t lists = (size_t)cap * (sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
+        x.tc_cap = tc_total - lists;
+        AL(x.d_tc_ws, x.tc_cap);
+        AL(x.d_tc, sizeof(TcCounters));
+        AL(x.d_tc_v, sizeof(int32_t) * (size_t)cap);
+        AL(x.d_tc_off, sizeof(int64_t) * (size_t)cap);
+    }
 #undef AL
     CK(cudaMemset(x.d_esc_count, 0, sizeof(int32_t) * 2));
     for (int i = 0; i < kNumBuckets; ++i) {
@@ -328,8 +365,9 @@ static int create_impl(gp_voxels_t* h)
     CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev));
     h->Gp = (c.grid_side + kQryBlk - 1) / kQryBlk * kQryBlk;
     h->gws_grid = 2 * h->sms;
-    const size_t need = solve_bytes(&c, h->sms, h->Gp) + store_bytes(&c);
-    if (c.mem_budget && need > c.mem_budget) return GPV_EBUDGET;
+    const size_t need_rest = solve_bytes(&c, h->sms, h->Gp) + store_bytes(&c);
+    if (c.mem_budget && need_rest > c.mem_budget) return GPV_EBUDGET;
+    const size_t need_tc = tc_bytes(&c, h->Gp, need_rest);
     const size_t mv = (size_t)c.max_voxels;
     auto alloc = [&](void** p, size_t bytes) -> int {
         cudaError_t e = cudaMalloc(p, bytes);
@@ -345,7 +383,8 @@ static int create_impl(gp_voxels_t* h)
     AL(h->d_pl_next, sizeof(int32_t) * mv);
 #undef AL
     h->gws_stride = gws_slice_elems(c.max_points, c.grid_side, h->Gp);
-    if ((rc = ctx_create(h, h->main, c.max_voxels)) != GPV_OK) return rc;
+    if ((rc = ctx_create(h, h->main, c.max_voxels, need_tc)) != GPV_OK) return rc;
+    if (need_tc > 0) CK(var_tc_prepare());
     if (c.hash_capacity > 0) {
         h->sctx = new (std::nothrow) SolveCtx[c.scan_slots];
         if (!h->sctx) return GPV_ENOMEM;
@@ -430,6 +469,14 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     a.gws = x.d_gws; a.gws_stride = h->gws_stride;
     a.max_points = c.max_points;
     a.nmax_small_f64 = std::min(h->plan[PREC_F64].nmax_smem, c.max_points);
+    if (kind == PREC_FF && x.tc_cap > 0) {
+        a.tc_ws = x.d_tc_ws;
+        a.tc_cap = x.tc_cap;
+        a.tc = x.d_tc;
+        a.tc_v = x.d_tc_v;
+        a.tc_off = x.d_tc_off;
+        a.tc_nmax = std::min(std::min(kTcMaxN, c.max_points), h->plan[PREC_FF].nmax_smem);
+    }
     return a;
 }
 
@@ -459,6 +506,7 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         CK(cudaStreamSynchronize(s));
         CK(cudaMemsetAsync(h->d_pl_next, 0, sizeof(int32_t) * nvox, s));
         a.escalate = 0;
+        a.tc_ws = nullptr;  // each launch forms its own variance
         a.work_count = h->d_one;
         a.work_base = nullptr;
         for (int32_t v = 0; v < nvox; ++v) {
@@ -506,6 +554,10 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             CK(cudaEventRecord(x.ev_join[i], x.side[i]));
             CK(cudaStreamWaitEvent(s, x.ev_join[i], 0));
         }
+    if (a.tc_ws) {  // variance and Gaussians of the voxels the buckets queued
+        CK(launch_var_tc(a, h->sms, s));
+        ++h->last_launches;
+    }
     if (kind == PREC_FF) {
         // FP64 re-solve of the voxels that failed the conditioning check
         a.escalate = 0;
@@ -972,6 +1024,9 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
             float ms = 3.0e38f;
             for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel
                 CK(cudaMemsetAsync(x.d_next + b, 0, sizeof(int32_t), s));
+                if (a.tc)  // each timed launch starts from an empty workspace
+                    CK(cudaMemsetAsync(reinterpret_cast<unsigned char*>(a.tc) + 8, 0,
+                                       sizeof(TcCounters) - 8, s));
                 CK(cudaEventRecord(e0, s));
                 CK(launch_solve(kind, B.tri_smem, nt, a, grid, sp.total, s));
                 CK(cudaEventRecord(e1, s));

@@ -25,6 +25,15 @@ constexpr int kQryBlk = 4;      // queries per register tile
 constexpr int kMaxG = 32;       // largest query grid side
 constexpr int kNumBuckets = 12; // size buckets of the batched launch
 
+// Device counters of the tensor-core variance of one solve call: total = workspace bytes
+// all eligible voxels would need (summed when the call classifies its voxels; the call
+// takes the tensor-core variance only if it fits tc_cap, so the choice does not depend on
+// scheduling), used = bytes handed out, count = voxels queued, next = dequeue counter.
+struct TcCounters {
+    unsigned long long total, used;
+    int32_t count, next;
+};
+
 struct SolveArgs {
     // inputs (CSR batch of voxels)
     const float* xyz;
@@ -66,7 +75,29 @@ struct SolveArgs {
     int nmax_small_f64;  // escalated voxels up to this n take the shared-memory FP64 pass
     int percol_max;      // shared-memory voxels up to this n use the per-column factor/inverse
     int panel;           // panel width of the blocked factor: 4, 8 or 16
+    // tensor-core variance (float-float, shared-memory factor): the solve kernel leaves
+    // L^-1, the cross-covariance factors and the mean of each voxel in tc_ws and k_var_tc
+    // forms diag(Sigma*) and the Gaussians from them.  Null tc_ws: the solve kernel
+    // forms them itself.
+    unsigned char* tc_ws;
+    uint64_t tc_cap;     // bytes of tc_ws
+    TcCounters* tc;
+    int32_t* tc_v;       // voxels queued for k_var_tc (one entry per voxel at most)
+    int64_t* tc_off;     // their byte offsets in tc_ws
+    int tc_nmax;         // largest n that takes the tensor-core variance
 };
+
+// Largest n of the tensor-core variance: with 8-bit slices the FP32 sums of the four
+// exact accumulator levels stay below 2^24 grid units for n <= 170.
+constexpr int kTcMaxN = 160;
+
+// Workspace bytes of one voxel: packed L^-1, the factors (n G and n Gp) and the G^2
+// means, float-float, rounded up to 16 bytes.
+__host__ __device__ inline uint64_t tc_need_bytes(int n, int G, int Gp)
+{
+    const uint64_t e = (uint64_t)n * (n + 1) / 2 + (uint64_t)n * G + (uint64_t)n * Gp + (uint64_t)G * G;
+    return (8 * e + 15) & ~(uint64_t)15;
+}
 
 // Shared-memory plan of one CTA (bytes), identical on host and device.
 // Elements of the working type in one CTA's global-workspace slice (factor + factors).
@@ -148,6 +179,8 @@ cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& 
                          cudaStream_t s);
 cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out);
 cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm);
+cudaError_t launch_var_tc(const SolveArgs& a, int sms, cudaStream_t s);
+cudaError_t var_tc_prepare();
 cudaError_t launch_init(const float* mean, const float* var, const uint8_t* axis,
                         const float* centres, const float* sf2, const uint32_t* status,
                         int32_t nvox, float size, int G, int n_s, int n_r, int init_mode,

@@ -234,4 +234,7 @@ __device__ __forceinline__ ff acc_norm(ff a) { return fast_two_sum(a.hi, a.lo); 
 
 template <class T> __device__ __forceinline__ T zero() { return from_f<T>(0.f); }
 
+template <class T> struct is_ff { static constexpr bool value = false; };
+template <> struct is_ff<ff> { static constexpr bool value = true; };
+
 }  // namespace gpv

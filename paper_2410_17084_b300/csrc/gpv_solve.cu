@@ -759,6 +759,22 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         if (n <= A.percol_max) inv_percol_smem<T>(L, n);
         else inv_smem<T>(L, n, tmp);
     }
+    // ---- tensor-core variance: reserve this voxel's workspace (float-float only) ------
+    __shared__ long long s_tc_off;
+    bool tc = false;
+    if (is_ff<T>::value && TRI_SMEM && A.tc_ws != nullptr && n <= A.tc_nmax) {
+        if (tid == 0) {
+            long long off = -1;
+            const unsigned long long need = tc_need_bytes(n, G, Gp);
+            if (A.tc->total <= A.tc_cap) {
+                const unsigned long long o = atomicAdd(&A.tc->used, need);
+                if (o + need <= A.tc_cap) off = (long long)o;
+            }
+            s_tc_off = off;
+        }
+        __syncthreads();
+        tc = s_tc_off >= 0;
+    }
     __syncthreads();
 
     // ---- posterior variance at the inputs (per-point noise feedback, Sec. 3.3) -------
@@ -856,8 +872,17 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         al[i] = (acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3]));
     }
 
+    // ---- A8 handed over: L^-1 and the factors go to the workspace, k_var_tc forms the
+    // variance on the tensor cores ------------------------------------------------------
+    const int ntri = n * (n + 1) / 2;
+    T* Wtc = tc ? reinterpret_cast<T*>(A.tc_ws + s_tc_off) : nullptr;
+    if (tc) {
+        for (int e = tid; e < ntri; e += nthr) Wtc[e] = L[e];
+        for (int e = tid; e < n * G; e += nthr) Wtc[ntri + e] = fa[e];
+        for (int e = tid; e < n * Gp; e += nthr) Wtc[ntri + n * G + e] = fb[e];
+    }
     // ---- A8: |X k_q|^2 by register-tiled contraction ------------------------------
-    {
+    if (!tc) {
         const int nqg = P.nqg, nrg = P.nrg;
         const int nb = (n + kRowBlk - 1) / kRowBlk;
         for (int w = tid; w < nqg * nrg; w += nthr) {
@@ -936,6 +961,11 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
                 acc_fma(s4[w], al[i + w] * fa[(i + w) * G + u], fb[(i + w) * Gp + vv]);
         for (; i < n; ++i) acc_fma(s4[0], al[i] * fa[i * G + u], fb[i * Gp + vv]);
         const T mu = m + ((acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3])));
+        if (tc) {
+            A.mean[obase + q] = to_f(mu);
+            Wtc[ntri + n * G + n * Gp + q] = mu;
+            continue;
+        }
         T nr = zero<T>();
         for (int g = 0; g < P.nrg; ++g) nr = nr + part[g * (G * Gp) + u * Gp + vv];
         T var = sf2 - nr;
@@ -948,6 +978,16 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         A.axis[v] = (uint8_t)axis;
         uint32_t st = A.escalation_pass ? VOX_ESCALATED : 0u;
         A.status[v] = st;
+    }
+    if (tc) {  // queue the voxel for k_var_tc
+        __syncthreads();
+        if (tid == 0) {
+            const int slot = atomicAdd(&A.tc->count, 1);
+            A.tc_v[slot] = v;
+            A.tc_off[slot] = s_tc_off;
+        }
+        __syncthreads();
+        return;
     }
     // ---- A10 (fused): Gaussians of the n_s x n_s subgrids ---------------------------
     if (want_init) {
@@ -1024,6 +1064,8 @@ __global__ void k_classify(SolveArgs A, const int* bucket_hi, int nb, int32_t* b
     for (int k = 0; k < nb; ++k)
         if (n <= bucket_hi[k]) { b = k; break; }
     atomicAdd(&bcount[b], 1);
+    if (A.tc_ws != nullptr && n <= A.tc_nmax)
+        atomicAdd(&A.tc->total, (unsigned long long)tc_need_bytes((int)n, A.G, A.Gp));
 }
 
 __global__ void k_scan(int nb, const int32_t* bcount, int32_t* bbase, int32_t* bcursor,
@@ -1063,6 +1105,8 @@ cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, in
 {
     cudaError_t e = cudaMemsetAsync(bcount, 0, sizeof(int32_t) * nb, s);
     if (e != cudaSuccess) return e;
+    if (a.tc != nullptr && (e = cudaMemsetAsync(a.tc, 0, sizeof(TcCounters), s)) != cudaSuccess)
+        return e;
     if (a.nvox > 0) {
         const int blk = 256, grd = (a.nvox + blk - 1) / blk;
         k_classify<<<grd, blk, 0, s>>>(a, bucket_hi, nb, bcount);

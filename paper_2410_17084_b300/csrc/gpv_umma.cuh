@@ -51,6 +51,16 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
            ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with BF16 operands and an FP32 accumulator, both
+// K-major: D format F32 (bits 4-5 = 1), A and B format BF16 (bits 7-9 and 10-12 = 1).
+// With 2-byte elements a core matrix row of 16 bytes holds 8 elements and one MMA
+// consumes K = 16, again two core matrices along K.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
 // ---- tensor memory ------------------------------------------------------------------
 // One warp allocates ncols columns (a power of two, >= 32) and writes the address into
 // shared memory; the same warp frees them.
@@ -91,6 +101,18 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u)
+        : "memory");
+}
+
+// D (tensor memory) = A * B^T (+ D when accumulate), BF16 operands, issued by one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, bool accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
         :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u)
         : "memory");
 }

@@ -1,0 +1,397 @@
+// gpv_vartc.cu -- diag(Sigma*) of Eq. 3 on the fifth-generation tensor cores for the
+// float-float path, var_q = sf2 - |L^-1 k_q|^2, followed by the Gaussians of Sec. 3.2
+// (Eq. 6-8).  The solve kernel leaves L^-1 (packed lower triangle, column-major), the
+// separable cross-covariance factors a_i(u), b_i(v) and the means of each voxel in a
+// workspace; this kernel forms V = L^-1 K* and its column norms.
+//
+// Precision.  Where points are dense, sf2 and |L^-1 k_q|^2 agree to about five digits,
+// so V needs some 48 significant bits, more than any single tensor-core product
+// carries.  The error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms
+// 59, 2012) gets them from BF16 products: every entry is cut into six slices of 8 bits on
+// a power-of-two grid shared by its row (row j of L^-1: 2^E_j > max_i |L^-1_ji|; the
+// column of query q in K*: 2^F_q > max_i |k_iq|).  Slice s of an entry is a multiple of
+// 2^(E - 8(s+1)) with at most 8 significant bits, so it is exactly a BF16 number, and a
+// product of two slices is exact in FP32.  All products of one level l = s + t lie on one
+// grid, and for l <= 3 the sum of their magnitudes over the pairs of the level and over
+// i stays below 2^24 grid units when n <= 160 (level 3: 6 * 2^14 n), so the tensor core's
+// FP32 accumulation of each of these levels is exact.  Levels 4 and 5 share a fifth
+// accumulator; its values stay near 2^-29 of 2^(E_j + F_q), so its FP32 rounding lies
+// about 2^-48 below that scale.  (A level's sum is not small: it reaches 2^19 of its own
+// grid, which is why level 3 needs an exact accumulator of its own.)  Pairs with
+// s + t > 5 are dropped (2^-48 as well).  V = L0 + ... + L4 is assembled and squared in
+// float-float.
+//
+// Organisation.  One persistent CTA per SM (256 threads) owns the tensor memory: five
+// accumulators of 128 lanes (the queries of one M tile) x up to 96 columns (rows j of
+// L^-1 per pass).  For each 16-wide chunk of i, all threads cut the A slices (K*^T: 128
+// queries x 16) and the B slices (L^-1: up to 96 rows x 16) into one of two shared-memory
+// buffers while the tensor core works on the other; one thread issues the 21 MMAs
+// (kind::f16, M = 128, N = rows of the pass, K = 16) and commits them to the buffer's
+// mbarrier.  The epilogue reads the accumulators with tcgen05.ld: lane = query, so each
+// thread sums its own query's norm with no cross-thread reduction.  Every wait is
+// bounded; a wait that gives up marks the voxel GPV_VOX_FAILED.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gpv_init.cuh"
+#include "gpv_internal.h"
+#include "gpv_num.cuh"
+#include "gpv_umma.cuh"
+
+namespace gpv {
+namespace {
+
+constexpr int kVT = 256;      // threads per CTA
+constexpr int kSl = 6;        // slices per operand entry
+constexpr int kLv = 5;        // accumulators: levels 0, 1, 2, 3 and 4..5
+constexpr int kMT = 128;      // queries per M tile (tensor-memory lanes)
+constexpr int kNJ = 96;       // rows of L^-1 per pass (MMA N; kLv * kNJ <= 512 columns)
+constexpr int kKC = 16;       // K of one MMA (BF16)
+constexpr int kSliceBytes = 128 * kKC * 2;  // one slice of a 128 x 16 operand chunk
+constexpr uint32_t kPolls = 1u << 26;
+
+// dynamic shared memory (bytes)
+constexpr int kOffA = 0;                                   // [2][kSl] A chunks
+constexpr int kOffB = kOffA + 2 * kSl * kSliceBytes;       // [2][kSl] B chunks
+constexpr int kOffEx = kOffB + 2 * kSl * kSliceBytes;      // int E_j [kTcMaxN]
+constexpr int kOffFq = kOffEx + 4 * kTcMaxN;               // int F_q [kMT]
+constexpr int kOffPm = kOffFq + 4 * kMT;                   // float partial maxima [kVT]
+constexpr int kOffNrm = kOffPm + 4 * kVT;                  // ff partial norms [2][kMT]
+constexpr int kOffMv = kOffNrm + 2 * kMT * 8;              // ff mean, var [2 G^2]
+// G <= 32; more than half an SM's shared memory, so one CTA per SM holds the tensor memory
+constexpr int kVarTcSmem = kOffMv + 2 * kMaxG * kMaxG * 8;
+
+__device__ __forceinline__ int tri_off_p(int c, int n) { return c * n - ((c * (c - 1)) >> 1); }
+
+// Smallest E with m < 2^E (m >= 0), kept where the slice grids stay normal FP32 numbers.
+__device__ __forceinline__ int exp_above(float m)
+{
+    if (!(m > 0.f)) return -100;
+    int e;
+    frexpf(m * 1.000001f, &e);  // margin for the rounding of the leading parts
+    return max(-100, min(100, e));
+}
+
+// Cut x = hi + lo (|x| < 2^E) into kSl slices on the grids 2^(E-8), ..., 2^(E-48):
+// round to the grid by adding and subtracting 1.5 * 2^(grid exponent + 23), keep the
+// exact remainder.  The first three slices come from hi alone; lo joins the remainder
+// for the last three (that FP32 sum errs by at most 2^(E-49)).  Returns the FP32 bit
+// patterns; each slice has at most 8 significant bits, so its upper half is its BF16.
+__device__ __forceinline__ void cut_slices(float hi, float lo, int E, uint32_t (&q)[kSl])
+{
+    float a = hi;
+#pragma unroll
+    for (int s = 0; s < kSl; ++s) {
+        if (s == 3) a = __fadd_rn(a, lo);
+        const float sig = __uint_as_float(((uint32_t)(E - 8 * s + 15 + 127) << 23) | 0x400000u);
+        const float t = __fsub_rn(__fadd_rn(a, sig), sig);
+        a = __fsub_rn(a, t);
+        q[s] = __float_as_uint(t);
+    }
+}
+
+// Byte offset of element (r, k) of a K-major, unswizzled BF16 chunk with 16 elements per
+// row: core matrices of 8 rows x 16 bytes, the two along K adjacent (LBO 128), 8-row
+// groups 256 bytes apart (SBO).
+__device__ __forceinline__ int kmaj16(int r, int k)
+{
+    return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// Slices of 8 consecutive K entries of one operand row, stored as one 16-byte row of
+// a core matrix in each of the kSl slice buffers.
+__device__ __forceinline__ void store_row8(unsigned char* buf, int r, int k0, const float (&hi)[8],
+                                           const float (&lo)[8], int E)
+{
+    uint32_t w[kSl][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        uint32_t a[kSl], b[kSl];
+        cut_slices(hi[2 * p], lo[2 * p], E, a);
+        cut_slices(hi[2 * p + 1], lo[2 * p + 1], E, b);
+#pragma unroll
+        for (int s = 0; s < kSl; ++s) w[s][p] = __byte_perm(a[s], b[s], 0x7632);
+    }
+    const int o = kmaj16(r, k0);
+#pragma unroll
+    for (int s = 0; s < kSl; ++s)
+        *reinterpret_cast<uint4*>(buf + s * kSliceBytes + o) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+}
+
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Ties the registers of a tcgen05.ld to a point after tcgen05.wait::ld: the compiler may
+// not read them before this (ordered) statement.
+__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16])
+{
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+
+// nrm += V^2 with V = l0 + ... + l4 (the levels of one entry of L^-1 K*): the exact levels
+// join the leading part by TwoSum, their errors and the merged tail the trailing part
+__device__ __forceinline__ void acc_levels(ff& nrm, float l0, float l1, float l2, float l3, float l4)
+{
+    const ff a = two_sum(l0, l1);
+    const ff b = two_sum(a.hi, l2);
+    const ff c = two_sum(b.hi, l3);
+    const ff V = ff_make(c.hi, __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), c.lo), l4));
+    acc_fma(nrm, V, V);
+}
+
+__device__ void write_failed(const SolveArgs& A, int v, int GG, float sf2f)
+{
+    for (int q = threadIdx.x; q < GG; q += blockDim.x) A.var[(int64_t)v * GG + q] = sf2f;
+    if (A.pos) {
+        const int NG = A.n_s * A.n_s;
+        for (int g = threadIdx.x; g < NG; g += blockDim.x) {
+            const int64_t o = (int64_t)v * NG + g;
+            for (int k = 0; k < 3; ++k) { A.pos[3 * o + k] = A.centres[3 * v + k]; A.scale[3 * o + k] = 0.f; }
+            A.quat[4 * o] = 1.f; A.quat[4 * o + 1] = 0.f; A.quat[4 * o + 2] = 0.f; A.quat[4 * o + 3] = 0.f;
+        }
+    }
+    if (threadIdx.x == 0) A.status[v] |= VOX_FAILED;
+}
+
+__global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    __shared__ int s_item;
+    __shared__ int s_broken;
+    __shared__ ff nodes[kMaxG];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int count = A.tc->count;
+    if (count == 0) return;
+    int* ex = reinterpret_cast<int*>(sm + kOffEx);
+    int* fq = reinterpret_cast<int*>(sm + kOffFq);
+    float* pm = reinterpret_cast<float*>(sm + kOffPm);
+    ff* nrm2 = reinterpret_cast<ff*>(sm + kOffNrm);
+    ff* mv = reinterpret_cast<ff*>(sm + kOffMv);
+    const int G = A.G, Gp = A.Gp, GG = G * G;
+    if (tid < G)
+        nodes[tid] = from_d<ff>(-0.5 * (double)A.size + ((double)tid + 0.5) * (double)A.size / (double)G);
+    if (warp == 0) umma::tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        umma::mbar_init(&mbar[0], 1);
+        umma::mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_broken = 0;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t abase = umma::smem_addr(sm + kOffA), bbase = umma::smem_addr(sm + kOffB);
+    uint32_t uses[2] = {0u, 0u};  // commits issued per buffer (identical in every thread)
+    int chunk = 0;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&A.tc->next, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= count) break;
+        const int v = A.tc_v[it];
+        const int n = (int)(A.offsets[v + 1] - A.offsets[v]);
+        const float sf2f = A.sf2[v];
+        if (s_broken) { write_failed(A, v, GG, sf2f); continue; }
+        const int ntri = n * (n + 1) / 2;
+        const ff* X = reinterpret_cast<const ff*>(A.tc_ws + A.tc_off[it]);
+        const ff* FA = X + ntri;
+        const ff* FB = FA + n * G;
+        const ff* MU = FB + n * Gp;
+
+        // row exponents of L^-1 (row j: entries (j, i), i <= j, one per packed column)
+        for (int j = tid; j < n; j += kVT) {
+            float m = 0.f;
+            for (int i = 0; i <= j; ++i) m = fmaxf(m, fabsf(X[tri_off_p(i, n) + j - i].hi));
+            ex[j] = exp_above(m);
+        }
+        bool failed = false;
+        const int r = tid & (kMT - 1), h = tid >> 7;  // operand row, half of the K chunk
+        for (int mt = 0; mt * kMT < GG && !failed; ++mt) {
+            const int q = mt * kMT + r;
+            const bool qv = q < GG;
+            const int u = qv ? q / G : 0, w = qv ? q - u * G : 0;
+            {   // query exponents (the two halves of the CTA split i)
+                float m = 0.f;
+                if (qv)
+                    for (int i = h; i < n; i += 2) m = fmaxf(m, fabsf(FA[i * G + u].hi * FB[i * Gp + w].hi));
+                pm[tid] = m;
+                __syncthreads();
+                if (tid < kMT) fq[tid] = exp_above(fmaxf(pm[tid], pm[tid + kMT]));
+                __syncthreads();
+            }
+            const int F = fq[r];
+            ff nrm = zero<ff>();
+            for (int j0 = 0; j0 < n && !failed; j0 += kNJ) {
+                const int nj = min(kNJ, n - j0), Np = (nj + 15) & ~15;
+                const int nkc = (min(n, j0 + nj) + kKC - 1) / kKC;  // rows j < j0 + nj need i <= j
+                const int j = j0 + r;
+                const int Ej = j < n ? ex[j] : 0;
+                uint32_t started = 0u;  // accumulators written in this pass (thread 0)
+                for (int kc = 0; kc < nkc; ++kc) {
+                    const int b = chunk & 1;
+                    if (uses[b] > 0) {  // the MMAs that last read this buffer are done
+                        const bool ok = umma::mbar_wait(&mbar[b], (uses[b] - 1) & 1, kPolls);
+                        if (__syncthreads_or(!ok)) { failed = true; break; }
+                    }
+                    unsigned char* abuf = sm + kOffA + b * kSl * kSliceBytes;
+                    unsigned char* bbuf = sm + kOffB + b * kSl * kSliceBytes;
+                    const int i0 = kc * kKC + 8 * h;
+                    {   // A: k(x_i, q) = a_i(u) b_i(v) for the 128 queries of the tile
+                        float hi[8], lo[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int i = i0 + e;
+                            ff k = zero<ff>();
+                            if (qv && i < n) k = FA[i * G + u] * FB[i * Gp + w];
+                            hi[e] = k.hi;
+                            lo[e] = k.lo;
+                        }
+                        store_row8(abuf, r, 8 * h, hi, lo, F);
+                    }
+                    {   // B: row j of L^-1, zero above the diagonal and past n
+                        float hi[8], lo[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int i = i0 + e;
+                            ff x = zero<ff>();
+                            if (j < n && i <= j) x = X[tri_off_p(i, n) + j - i];
+                            hi[e] = x.hi;
+                            lo[e] = x.lo;
+                        }
+                        store_row8(bbuf, r, 8 * h, hi, lo, Ej);
+                    }
+                    umma::fence_proxy_async_smem();
+                    __syncthreads();
+                    if (tid == 0) {
+                        umma::fence_after_sync();
+                        const uint32_t idesc = umma::idesc_bf16(kMT, Np);
+                        const uint32_t a0 = abase + b * kSl * kSliceBytes;
+                        const uint32_t b0 = bbase + b * kSl * kSliceBytes;
+#pragma unroll
+                        for (int s = 0; s < kSl; ++s)
+#pragma unroll
+                            for (int t = 0; s + t < kSl; ++t) {
+                                const int lv = min(s + t, kLv - 1);
+                                const bool acc = (started >> lv) & 1u;
+                                started |= 1u << lv;
+                                umma::mma_bf16(tmem + lv * kNJ, umma::make_desc(a0 + t * kSliceBytes, 128, 256),
+                                               umma::make_desc(b0 + s * kSliceBytes, 128, 256), idesc, acc);
+                            }
+                        umma::mma_commit(&mbar[b]);
+                    }
+                    ++uses[b];
+                    ++chunk;
+                }
+                if (failed) break;
+                {   // all MMAs of the pass are done once its last commit has arrived
+                    const int lb = (chunk - 1) & 1;
+                    const bool ok = umma::mbar_wait(&mbar[lb], (uses[lb] - 1) & 1, kPolls);
+                    if (__syncthreads_or(!ok)) { failed = true; break; }
+                }
+                umma::fence_after_sync();
+                {   // epilogue: warps w and w + 4 read lanes 32 (w % 4) .., halves of the columns
+                    const int grp = warp >> 2;
+                    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+                    const int U = Np / 16, uh = (U + 1) / 2;
+                    const int ua = grp ? uh : 0, ub = grp ? U : uh;
+                    for (int uu = ua; uu < ub; ++uu) {
+                        uint32_t l[kLv][16];
+#pragma unroll
+                        for (int lv = 0; lv < kLv; ++lv)
+                            tmem_ld16_nowait(tmem + lane_base + lv * kNJ + uu * 16, l[lv]);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int lv = 0; lv < kLv; ++lv) reg_fence16(l[lv]);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            if (j0 + uu * 16 + c < n)
+                                acc_levels(nrm, __uint_as_float(l[0][c]), __uint_as_float(l[1][c]),
+                                           __uint_as_float(l[2][c]), __uint_as_float(l[3][c]),
+                                           __uint_as_float(l[4][c]));
+                    }
+                }
+                umma::fence_before_sync();
+                __syncthreads();
+            }
+            if (failed) break;
+            // the two column halves of each query -> variance
+            {
+                const int row = 32 * (warp & 3) + lane, grp = warp >> 2;
+                nrm2[grp * kMT + row] = acc_norm(nrm);
+                __syncthreads();
+                if (tid < kMT) {
+                    const int qq = mt * kMT + tid;
+                    if (qq < GG) {
+                        const ff tot = nrm2[tid] + nrm2[kMT + tid];
+                        ff var = from_f<ff>(sf2f) - tot;
+                        if (!(var.hi > 0.f)) var = zero<ff>();
+                        A.var[(int64_t)v * GG + qq] = to_f(var);
+                        mv[qq] = MU[qq];
+                        mv[GG + qq] = var;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (failed) {
+            if (tid == 0) s_broken = 1;
+            __syncthreads();
+            write_failed(A, v, GG, sf2f);
+            continue;
+        }
+        // ---- A10: Gaussians of the n_s x n_s subgrids (Eq. 6-8) ------------------------
+        if (A.pos) {
+            const int NG = A.n_s * A.n_s;
+            const int axis = A.axis[v];
+            for (int g = tid; g < NG; g += kVT) {
+                const int64_t o = (int64_t)v * NG + g;
+                init_one_gaussian<ff>(mv, mv + GG, nodes, axis, A.centres + 3 * v, A.size, G, A.n_s,
+                                      A.n_r, sf2f, A.init_mode, g / A.n_s, g % A.n_s, A.pos + 3 * o,
+                                      A.scale + 3 * o, A.quat + 4 * o);
+            }
+        }
+        __syncthreads();
+    }
+    // a pass that gave up may have MMAs in flight: wait for them (bounded) before freeing
+    if (s_broken) {
+        for (int b = 0; b < 2; ++b)
+            if (uses[b] > 0) umma::mbar_wait(&mbar[b], (uses[b] - 1) & 1, kPolls);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 0) umma::tmem_free(tmem, 512);
+}
+
+}  // namespace
+
+cudaError_t var_tc_prepare()
+{
+    return cudaFuncSetAttribute(k_var_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kVarTcSmem);
+}
+
+cudaError_t launch_var_tc(const SolveArgs& a, int sms, cudaStream_t s)
+{
+    k_var_tc<<<sms, kVT, kVarTcSmem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gpv

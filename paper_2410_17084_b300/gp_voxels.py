@@ -61,6 +61,7 @@ class gp_voxels_config(ctypes.Structure):
         ("eta", ctypes.c_float),
         ("noise_floor", ctypes.c_float),
         ("factor_panel", ctypes.c_int),
+        ("tc_workspace_mb", ctypes.c_int),
     ]
 
 
