@@ -114,7 +114,8 @@ def ff_peak_tflops(sm_mhz: float) -> float:
     return 148 * 128 * sm_mhz * 1e6 / FF_OPS_PER_FMA * 2 / 1e12
 
 
-SOLVE_KERNEL_SOURCES = ("gpv_init.cuh", "gpv_internal.h", "gpv_num.cuh", "gpv_solve.cu")
+SOLVE_KERNEL_SOURCES = ("gpv_init.cuh", "gpv_internal.h", "gpv_num.cuh", "gpv_solve.cu", "gpv_umma.cuh",
+                        "gpv_vartc.cu")
 
 
 def traffic_from_profiles(nvox_step: int):
@@ -563,7 +564,9 @@ def main():
                                   "multiply-add x 2 flops (derived from unit counts and the "
                                   "maximum clock); achieved = algorithmic FLOPs of the step "
                                   "(n^3/3 + n^2 G^2 + 4 n G^2 + 4 n^2 per voxel) / step time, "
-                                  "the solve kernels of all size buckets running concurrently",
+                                  "the solve kernels of all size buckets running concurrently, "
+                                  "then the tensor-core variance kernel (its BF16 slice "
+                                  "products are not counted: only the algorithmic FLOPs are)",
                      "measured_fp32_tflops": meas_fp32,
                      "measured_ff_tflops": meas_ff,
                      "frac_of_measured_ff": achieved / meas_ff},

@@ -557,6 +557,10 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     if (a.tc_ws) {  // variance and Gaussians of the voxels the buckets queued
         CK(launch_var_tc(a, h->sms, s));
         ++h->last_launches;
+        if (a.pos) {
+            CK(launch_init_tc(a, h->sms, s));
+            ++h->last_launches;
+        }
     }
     if (kind == PREC_FF) {
         // FP64 re-solve of the voxels that failed the conditioning check

@@ -91,12 +91,13 @@ struct SolveArgs {
 // exact accumulator levels stay below 2^24 grid units for n <= 170.
 constexpr int kTcMaxN = 160;
 
-// Workspace bytes of one voxel: packed L^-1, the factors (n G and n Gp) and the G^2
-// means, float-float, rounded up to 16 bytes.
+// Workspace bytes of one voxel: packed L^-1, the factors (n G and n Gp), the G^2 means
+// and the G^2 variances, float-float, then the slice exponents of the n rows of L^-1 and
+// of the G^2 queries (int32), rounded up to 16 bytes.
 __host__ __device__ inline uint64_t tc_need_bytes(int n, int G, int Gp)
 {
-    const uint64_t e = (uint64_t)n * (n + 1) / 2 + (uint64_t)n * G + (uint64_t)n * Gp + (uint64_t)G * G;
-    return (8 * e + 15) & ~(uint64_t)15;
+    const uint64_t e = (uint64_t)n * (n + 1) / 2 + (uint64_t)n * G + (uint64_t)n * Gp + 2 * (uint64_t)G * G;
+    return (8 * e + 4 * ((uint64_t)n + (uint64_t)G * G) + 15) & ~(uint64_t)15;
 }
 
 // Shared-memory plan of one CTA (bytes), identical on host and device.
@@ -180,6 +181,7 @@ cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& 
 cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out);
 cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm);
 cudaError_t launch_var_tc(const SolveArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_init_tc(const SolveArgs& a, int sms, cudaStream_t s);
 cudaError_t var_tc_prepare();
 cudaError_t launch_init(const float* mean, const float* var, const uint8_t* axis,
                         const float* centres, const float* sf2, const uint32_t* status,

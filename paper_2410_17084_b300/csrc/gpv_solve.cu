@@ -880,6 +880,19 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         for (int e = tid; e < ntri; e += nthr) Wtc[e] = L[e];
         for (int e = tid; e < n * G; e += nthr) Wtc[ntri + e] = fa[e];
         for (int e = tid; e < n * Gp; e += nthr) Wtc[ntri + n * G + e] = fb[e];
+        // slice exponents: rows j of L^-1 and queries (u, v) of K* = a(u) b(v)
+        int* EX = reinterpret_cast<int*>(Wtc + ntri + n * G + n * Gp + 2 * GG);
+        for (int j = tid; j < n; j += nthr) {
+            float mx = 0.f;
+            for (int i = 0; i <= j; ++i) mx = fmaxf(mx, fabsf(hi_of(L[tri_off(i, n) + j - i])));
+            EX[j] = tc_exp_above(mx);
+        }
+        for (int q = tid; q < GG; q += nthr) {
+            const int u = q / G, vq = q - u * G;
+            float mx = 0.f;
+            for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(hi_of(fa[i * G + u]) * hi_of(fb[i * Gp + vq])));
+            EX[n + q] = tc_exp_above(mx);
+        }
     }
     // ---- A8: |X k_q|^2 by register-tiled contraction ------------------------------
     if (!tc) {

@@ -41,36 +41,27 @@
 namespace gpv {
 namespace {
 
-constexpr int kVT = 256;      // threads per CTA
+constexpr int kVT = 512;      // threads per CTA
 constexpr int kSl = 6;        // slices per operand entry
 constexpr int kLv = 5;        // accumulators: levels 0, 1, 2, 3 and 4..5
 constexpr int kMT = 128;      // queries per M tile (tensor-memory lanes)
 constexpr int kNJ = 96;       // rows of L^-1 per pass (MMA N; kLv * kNJ <= 512 columns)
 constexpr int kKC = 16;       // K of one MMA (BF16)
 constexpr int kSliceBytes = 128 * kKC * 2;  // one slice of a 128 x 16 operand chunk
+constexpr int kParts = kVT / kMT;             // threads per operand row (K chunk split)
+constexpr int kKE = kKC / kParts;             // K entries per thread and chunk
 constexpr uint32_t kPolls = 1u << 26;
 
 // dynamic shared memory (bytes)
 constexpr int kOffA = 0;                                   // [2][kSl] A chunks
 constexpr int kOffB = kOffA + 2 * kSl * kSliceBytes;       // [2][kSl] B chunks
-constexpr int kOffEx = kOffB + 2 * kSl * kSliceBytes;      // int E_j [kTcMaxN]
-constexpr int kOffFq = kOffEx + 4 * kTcMaxN;               // int F_q [kMT]
-constexpr int kOffPm = kOffFq + 4 * kMT;                   // float partial maxima [kVT]
-constexpr int kOffNrm = kOffPm + 4 * kVT;                  // ff partial norms [2][kMT]
-constexpr int kOffMv = kOffNrm + 2 * kMT * 8;              // ff mean, var [2 G^2]
-// G <= 32; more than half an SM's shared memory, so one CTA per SM holds the tensor memory
-constexpr int kVarTcSmem = kOffMv + 2 * kMaxG * kMaxG * 8;
+constexpr int kOffNrm = kOffB + 2 * kSl * kSliceBytes;     // ff partial norms [kParts][kMT]
+constexpr int kOffEnd = kOffNrm + kParts * kMT * 8;
+// at least 120 KB, more than half an SM's shared memory, so that one CTA per SM holds
+// the tensor memory
+constexpr int kVarTcSmem = kOffEnd > 120 * 1024 ? kOffEnd : 120 * 1024;
 
 __device__ __forceinline__ int tri_off_p(int c, int n) { return c * n - ((c * (c - 1)) >> 1); }
-
-// Smallest E with m < 2^E (m >= 0), kept where the slice grids stay normal FP32 numbers.
-__device__ __forceinline__ int exp_above(float m)
-{
-    if (!(m > 0.f)) return -100;
-    int e;
-    frexpf(m * 1.000001f, &e);  // margin for the rounding of the leading parts
-    return max(-100, min(100, e));
-}
 
 // Cut x = hi + lo (|x| < 2^E) into kSl slices on the grids 2^(E-8), ..., 2^(E-48):
 // round to the grid by adding and subtracting 1.5 * 2^(grid exponent + 23), keep the
@@ -98,14 +89,15 @@ __device__ __forceinline__ int kmaj16(int r, int k)
     return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// Slices of 8 consecutive K entries of one operand row, stored as one 16-byte row of
-// a core matrix in each of the kSl slice buffers.
-__device__ __forceinline__ void store_row8(unsigned char* buf, int r, int k0, const float (&hi)[8],
-                                           const float (&lo)[8], int E)
+// Slices of NE (4 or 8) consecutive K entries of one operand row, stored in each of the
+// kSl slice buffers as NE * 2 bytes of a core-matrix row.
+template <int NE>
+__device__ __forceinline__ void store_row(unsigned char* buf, int r, int k0, const float (&hi)[NE],
+                                          const float (&lo)[NE], int E)
 {
-    uint32_t w[kSl][4];
+    uint32_t w[kSl][NE / 2];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < NE / 2; ++p) {
         uint32_t a[kSl], b[kSl];
         cut_slices(hi[2 * p], lo[2 * p], E, a);
         cut_slices(hi[2 * p + 1], lo[2 * p + 1], E, b);
@@ -114,18 +106,20 @@ __device__ __forceinline__ void store_row8(unsigned char* buf, int r, int k0, co
     }
     const int o = kmaj16(r, k0);
 #pragma unroll
-    for (int s = 0; s < kSl; ++s)
-        *reinterpret_cast<uint4*>(buf + s * kSliceBytes + o) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    for (int s = 0; s < kSl; ++s) {
+        if constexpr (NE == 8)
+            *reinterpret_cast<uint4*>(buf + s * kSliceBytes + o) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+        else
+            *reinterpret_cast<uint2*>(buf + s * kSliceBytes + o) = make_uint2(w[s][0], w[s][1]);
+    }
 }
 
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8])
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[6]), "=r"(r[7])
         : "r"(taddr));
 }
 
@@ -133,12 +127,18 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // Ties the registers of a tcgen05.ld to a point after tcgen05.wait::ld: the compiler may
 // not read them before this (ordered) statement.
-__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16])
+__device__ __forceinline__ void reg_fence8(uint32_t (&r)[8])
 {
     asm volatile(""
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+                   "+r"(r[6]), "+r"(r[7]));
+}
+
+// Pulls a voxel's workspace (bytes from p) toward L2 while the CTA works on another voxel.
+__device__ __forceinline__ void prefetch_l2(const unsigned char* p, uint64_t bytes)
+{
+    for (uint64_t o = (uint64_t)threadIdx.x * 128; o < bytes; o += (uint64_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" :: "l"(p + o));
 }
 
 // nrm += V^2 with V = l0 + ... + l4 (the levels of one entry of L^-1 K*): the exact levels
@@ -171,20 +171,13 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tslot;
-    __shared__ int s_item;
+    __shared__ int s_item, s_next;
     __shared__ int s_broken;
-    __shared__ ff nodes[kMaxG];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int count = A.tc->count;
     if (count == 0) return;
-    int* ex = reinterpret_cast<int*>(sm + kOffEx);
-    int* fq = reinterpret_cast<int*>(sm + kOffFq);
-    float* pm = reinterpret_cast<float*>(sm + kOffPm);
     ff* nrm2 = reinterpret_cast<ff*>(sm + kOffNrm);
-    ff* mv = reinterpret_cast<ff*>(sm + kOffMv);
     const int G = A.G, Gp = A.Gp, GG = G * G;
-    if (tid < G)
-        nodes[tid] = from_d<ff>(-0.5 * (double)A.size + ((double)tid + 0.5) * (double)A.size / (double)G);
     if (warp == 0) umma::tmem_alloc(&tslot, 512);
     if (tid == 0) {
         umma::mbar_init(&mbar[0], 1);
@@ -199,51 +192,53 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
     const uint32_t abase = umma::smem_addr(sm + kOffA), bbase = umma::smem_addr(sm + kOffB);
     uint32_t uses[2] = {0u, 0u};  // commits issued per buffer (identical in every thread)
     int chunk = 0;
+    if (tid == 0) s_item = atomicAdd(&A.tc->next, 1);
+    __syncthreads();
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(&A.tc->next, 1);
-        __syncthreads();
         const int it = s_item;
-        __syncthreads();
         if (it >= count) break;
+        if (tid == 0) s_next = atomicAdd(&A.tc->next, 1);  // one voxel ahead
         const int v = A.tc_v[it];
         const int n = (int)(A.offsets[v + 1] - A.offsets[v]);
         const float sf2f = A.sf2[v];
-        if (s_broken) { write_failed(A, v, GG, sf2f); continue; }
+        __syncthreads();
+        {   // the next voxel's workspace travels to L2 meanwhile
+            const int nx = s_next;
+            if (nx < count) {
+                const int vn = A.tc_v[nx];
+                const int nn = (int)(A.offsets[vn + 1] - A.offsets[vn]);
+                prefetch_l2(A.tc_ws + A.tc_off[nx], tc_need_bytes(nn, G, Gp));
+            }
+        }
+        if (s_broken) {
+            write_failed(A, v, GG, sf2f);
+            __syncthreads();
+            if (tid == 0) s_item = s_next;
+            __syncthreads();
+            continue;
+        }
         const int ntri = n * (n + 1) / 2;
         const ff* X = reinterpret_cast<const ff*>(A.tc_ws + A.tc_off[it]);
         const ff* FA = X + ntri;
         const ff* FB = FA + n * G;
         const ff* MU = FB + n * Gp;
-
-        // row exponents of L^-1 (row j: entries (j, i), i <= j, one per packed column)
-        for (int j = tid; j < n; j += kVT) {
-            float m = 0.f;
-            for (int i = 0; i <= j; ++i) m = fmaxf(m, fabsf(X[tri_off_p(i, n) + j - i].hi));
-            ex[j] = exp_above(m);
-        }
+        ff* VAR = const_cast<ff*>(MU) + GG;
+        const int* EX = reinterpret_cast<const int*>(VAR + GG);  // slice exponents: rows of
+        const int* FQ = EX + n;                                  // L^-1, then the queries
         bool failed = false;
-        const int r = tid & (kMT - 1), h = tid >> 7;  // operand row, half of the K chunk
+        const int r = tid & (kMT - 1), h = tid >> 7;  // operand row, part of the K chunk
         for (int mt = 0; mt * kMT < GG && !failed; ++mt) {
             const int q = mt * kMT + r;
             const bool qv = q < GG;
             const int u = qv ? q / G : 0, w = qv ? q - u * G : 0;
-            {   // query exponents (the two halves of the CTA split i)
-                float m = 0.f;
-                if (qv)
-                    for (int i = h; i < n; i += 2) m = fmaxf(m, fabsf(FA[i * G + u].hi * FB[i * Gp + w].hi));
-                pm[tid] = m;
-                __syncthreads();
-                if (tid < kMT) fq[tid] = exp_above(fmaxf(pm[tid], pm[tid + kMT]));
-                __syncthreads();
-            }
-            const int F = fq[r];
+            const int F = qv ? FQ[q] : 0;
             ff nrm = zero<ff>();
             for (int j0 = 0; j0 < n && !failed; j0 += kNJ) {
                 const int nj = min(kNJ, n - j0), Np = (nj + 15) & ~15;
                 const int nkc = (min(n, j0 + nj) + kKC - 1) / kKC;  // rows j < j0 + nj need i <= j
                 const int j = j0 + r;
-                const int Ej = j < n ? ex[j] : 0;
+                const int Ej = j < n ? EX[j] : 0;
                 uint32_t started = 0u;  // accumulators written in this pass (thread 0)
                 for (int kc = 0; kc < nkc; ++kc) {
                     const int b = chunk & 1;
@@ -253,30 +248,30 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                     }
                     unsigned char* abuf = sm + kOffA + b * kSl * kSliceBytes;
                     unsigned char* bbuf = sm + kOffB + b * kSl * kSliceBytes;
-                    const int i0 = kc * kKC + 8 * h;
+                    const int i0 = kc * kKC + kKE * h;
                     {   // A: k(x_i, q) = a_i(u) b_i(v) for the 128 queries of the tile
-                        float hi[8], lo[8];
+                        float hi[kKE], lo[kKE];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
+                        for (int e = 0; e < kKE; ++e) {
                             const int i = i0 + e;
                             ff k = zero<ff>();
                             if (qv && i < n) k = FA[i * G + u] * FB[i * Gp + w];
                             hi[e] = k.hi;
                             lo[e] = k.lo;
                         }
-                        store_row8(abuf, r, 8 * h, hi, lo, F);
+                        store_row<kKE>(abuf, r, kKE * h, hi, lo, F);
                     }
                     {   // B: row j of L^-1, zero above the diagonal and past n
-                        float hi[8], lo[8];
+                        float hi[kKE], lo[kKE];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
+                        for (int e = 0; e < kKE; ++e) {
                             const int i = i0 + e;
                             ff x = zero<ff>();
                             if (j < n && i <= j) x = X[tri_off_p(i, n) + j - i];
                             hi[e] = x.hi;
                             lo[e] = x.lo;
                         }
-                        store_row8(bbuf, r, 8 * h, hi, lo, Ej);
+                        store_row<kKE>(bbuf, r, kKE * h, hi, lo, Ej);
                     }
                     umma::fence_proxy_async_smem();
                     __syncthreads();
@@ -307,22 +302,21 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                     if (__syncthreads_or(!ok)) { failed = true; break; }
                 }
                 umma::fence_after_sync();
-                {   // epilogue: warps w and w + 4 read lanes 32 (w % 4) .., halves of the columns
+                {   // epilogue: warps w, w + 4, .. read lanes 32 (w % 4) ..; 8-column units round robin
                     const int grp = warp >> 2;
                     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-                    const int U = Np / 16, uh = (U + 1) / 2;
-                    const int ua = grp ? uh : 0, ub = grp ? U : uh;
-                    for (int uu = ua; uu < ub; ++uu) {
-                        uint32_t l[kLv][16];
+                    const int U = Np / 8;
+                    for (int uu = grp; uu < U; uu += kParts) {
+                        uint32_t l[kLv][8];
 #pragma unroll
                         for (int lv = 0; lv < kLv; ++lv)
-                            tmem_ld16_nowait(tmem + lane_base + lv * kNJ + uu * 16, l[lv]);
+                            tmem_ld8_nowait(tmem + lane_base + lv * kNJ + uu * 8, l[lv]);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int lv = 0; lv < kLv; ++lv) reg_fence16(l[lv]);
+                        for (int lv = 0; lv < kLv; ++lv) reg_fence8(l[lv]);
 #pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            if (j0 + uu * 16 + c < n)
+                        for (int c = 0; c < 8; ++c)
+                            if (j0 + uu * 8 + c < n)
                                 acc_levels(nrm, __uint_as_float(l[0][c]), __uint_as_float(l[1][c]),
                                            __uint_as_float(l[2][c]), __uint_as_float(l[3][c]),
                                            __uint_as_float(l[4][c]));
@@ -340,12 +334,13 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                 if (tid < kMT) {
                     const int qq = mt * kMT + tid;
                     if (qq < GG) {
-                        const ff tot = nrm2[tid] + nrm2[kMT + tid];
+                        ff tot = nrm2[tid];
+#pragma unroll
+                        for (int g = 1; g < kParts; ++g) tot = tot + nrm2[g * kMT + tid];
                         ff var = from_f<ff>(sf2f) - tot;
                         if (!(var.hi > 0.f)) var = zero<ff>();
                         A.var[(int64_t)v * GG + qq] = to_f(var);
-                        mv[qq] = MU[qq];
-                        mv[GG + qq] = var;
+                        VAR[qq] = var;  // for the Gaussians (k_init_tc)
                     }
                 }
                 __syncthreads();
@@ -355,19 +350,13 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
             if (tid == 0) s_broken = 1;
             __syncthreads();
             write_failed(A, v, GG, sf2f);
+            __syncthreads();
+            if (tid == 0) s_item = s_next;
+            __syncthreads();
             continue;
         }
-        // ---- A10: Gaussians of the n_s x n_s subgrids (Eq. 6-8) ------------------------
-        if (A.pos) {
-            const int NG = A.n_s * A.n_s;
-            const int axis = A.axis[v];
-            for (int g = tid; g < NG; g += kVT) {
-                const int64_t o = (int64_t)v * NG + g;
-                init_one_gaussian<ff>(mv, mv + GG, nodes, axis, A.centres + 3 * v, A.size, G, A.n_s,
-                                      A.n_r, sf2f, A.init_mode, g / A.n_s, g % A.n_s, A.pos + 3 * o,
-                                      A.scale + 3 * o, A.quat + 4 * o);
-            }
-        }
+        __syncthreads();
+        if (tid == 0) s_item = s_next;
         __syncthreads();
     }
     // a pass that gave up may have MMAs in flight: wait for them (bounded) before freeing
@@ -381,7 +370,42 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
     if (warp == 0) umma::tmem_free(tmem, 512);
 }
 
+// ---- A10: Gaussians of the n_s x n_s subgrids (Eq. 6-8) of the voxels k_var_tc served:
+// one warp per voxel, lanes over the Gaussians, the float-float means and variances read
+// from the workspace (many warps per SM hide the latency of the small eigenproblems).
+__global__ void __launch_bounds__(256) k_init_tc(SolveArgs A)
+{
+    __shared__ ff nodes[kMaxG];
+    const int G = A.G, Gp = A.Gp, GG = G * G, NG = A.n_s * A.n_s;
+    if (threadIdx.x < G)
+        nodes[threadIdx.x] = from_d<ff>(-0.5 * (double)A.size + ((double)threadIdx.x + 0.5) * (double)A.size / (double)G);
+    __syncthreads();
+    const int count = A.tc->count;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < count; it += nwarps) {
+        const int v = A.tc_v[it];
+        if (A.status[v] & VOX_FAILED) continue;  // k_var_tc wrote the prior and default Gaussians
+        const int n = (int)(A.offsets[v + 1] - A.offsets[v]);
+        const ff* MU = reinterpret_cast<const ff*>(A.tc_ws + A.tc_off[it]) + n * (n + 1) / 2 + n * G + n * Gp;
+        const int axis = A.axis[v];
+        const float sf2f = A.sf2[v];
+        for (int g = lane; g < NG; g += 32) {
+            const int64_t o = (int64_t)v * NG + g;
+            init_one_gaussian<ff>(MU, MU + GG, nodes, axis, A.centres + 3 * v, A.size, G, A.n_s, A.n_r,
+                                  sf2f, A.init_mode, g / A.n_s, g % A.n_s, A.pos + 3 * o, A.scale + 3 * o,
+                                  A.quat + 4 * o);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_init_tc(const SolveArgs& a, int sms, cudaStream_t s)
+{
+    k_init_tc<<<sms * 4, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t var_tc_prepare()
 {

@@ -88,7 +88,7 @@ def test_tc_quadric_against_oracle_and_cuda_cores(gpv, oracle):
     b = _quadric(600, seed=31)
     tc, l_tc = _run(gpv, b)
     cc, l_cc = _run(gpv, b, tc_workspace_mb=0)
-    assert l_tc == l_cc + 1  # k_var_tc ran
+    assert l_tc == l_cc + 2  # k_var_tc and k_init_tc ran
     solved = _oracle_check(b, tc, oracle, "tc quadric G=16")
     _agree(b, tc, cc, solved, "tc quadric G=16")
 
@@ -106,7 +106,7 @@ def test_tc_grid_sides(gpv, oracle, shape):
     b = full.subset(idx)
     tc, l_tc = _run(gpv, b)
     cc, l_cc = _run(gpv, b, tc_workspace_mb=0)
-    assert l_tc == l_cc + 1
+    assert l_tc == l_cc + 2
     solved = _oracle_check(b, tc, oracle, f"tc {shape}")
     _agree(b, tc, cc, solved, f"tc {shape}")
 
