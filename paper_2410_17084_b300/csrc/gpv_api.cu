@@ -35,6 +35,13 @@ int cuda_fail(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
+// Launch configuration of the solve variant that hands the variance to the tensor cores
+struct VarCfg {
+    int nthr = 0, smem = 0, grid = 0;
+    bool percol = false;
+    int panel = 16;
+};
+
 struct Bucket {
     int hi;        // largest n of the bucket
     int nthr;      // CTA size
@@ -43,6 +50,8 @@ struct Bucket {
     bool tri_smem; // factor in shared memory (else in the global workspace slice)
     bool percol;   // per-column (not blocked) factor and inverse
     int panel;     // panel width of the blocked factor (4, 8, 16)
+    bool tcv_ok;   // float-float bucket whose voxels all take the tensor-core variance
+    VarCfg v;      // its launch configuration in that case
 };
 
 struct PrecPlan {
@@ -50,6 +59,8 @@ struct PrecPlan {
     Bucket b[kNumBuckets];
     int* d_hi = nullptr;  // device copy of the bucket upper bounds
     int nmax_smem = 0;
+    int tc_nmax = 0;      // largest n of the tensor-core variance (0: off)
+    int fb_smem = 0, fb_grid = 0;  // regular re-solve of what the variant could not hand over
 };
 
 // Work queues, workspace and streams of one solve in flight.  The CSR entry owns one;
@@ -70,6 +81,7 @@ struct SolveCtx {
     TcCounters* d_tc = nullptr;
     int32_t* d_tc_v = nullptr;
     int64_t* d_tc_off = nullptr;
+    int32_t* d_tc_fb = nullptr;
     cudaStream_t side[kNumBuckets] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kNumBuckets] = {};
@@ -198,6 +210,31 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         CK(solve_occupancy(kind, B.tri_smem, B.nthr, B.smem, &occ));
         if (occ < 1) return GPV_EINVAL;
         B.grid = B.tri_smem ? h->sms * occ : h->gws_grid;
+        B.tcv_ok = false;
+    }
+    // tensor-core variance (batch entry, float-float): the variant without the contraction
+    // for every shared-memory bucket up to its largest n
+    P.tc_nmax = 0;
+    if (kind == PREC_FF && h->main.tc_cap > 0) {
+        P.tc_nmax = std::min(std::min(kTcMaxN, c.max_points), P.nmax_smem);
+        for (int i = 0; i < P.nb; ++i) {
+            Bucket& B = P.b[i];
+            if (!B.tri_smem || B.hi > P.tc_nmax) continue;
+            B.tcv_ok = true;
+            B.v.nthr = B.nthr;
+            B.v.percol = B.percol;
+            B.v.panel = B.panel;
+            B.v.smem = smem_plan(B.hi, c.grid_side, h->Gp, 8, true, B.v.nthr, true).total;
+            int occ = 0;
+            CK(solve_occupancy(kind, true, B.v.nthr, B.v.smem, &occ, true));
+            if (occ < 1) return GPV_EINVAL;
+            B.v.grid = h->sms * occ;
+        }
+        P.fb_smem = smem_plan(P.tc_nmax, c.grid_side, h->Gp, 8, true, 512).total;
+        int occ = 0;
+        CK(solve_occupancy(kind, true, 512, P.fb_smem, &occ));
+        if (occ < 1) return GPV_EINVAL;
+        P.fb_grid = h->sms * occ;
     }
     CK(cudaMalloc(&P.d_hi, sizeof(int) * kNumBuckets));
     CK(cudaMemcpy(P.d_hi, hi_host, sizeof(int) * P.nb, cudaMemcpyHostToDevice));
@@ -250,7 +287,7 @@ static size_t tc_bytes(const gp_voxels_config* c, int Gp, size_t rest)
     const int nmax = std::min(kTcMaxN, c->max_points);
     size_t b = std::min((size_t)c->tc_workspace_mb << 20,
                         (size_t)c->max_voxels * (size_t)tc_need_bytes(nmax, c->grid_side, Gp));
-    b += (size_t)c->max_voxels * (sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
+    b += (size_t)c->max_voxels * (2 * sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
     if (c->mem_budget) b = c->mem_budget > rest ? std::min(b, c->mem_budget - rest) : 0;
     return b < ((size_t)16 << 20) ? 0 : b;
 }
@@ -284,7 +321,7 @@ static void ctx_release(SolveCtx& x)
 {
     cudaFree(x.d_bcount); cudaFree(x.d_bbase); cudaFree(x.d_bcursor); cudaFree(x.d_next);
     cudaFree(x.d_work); cudaFree(x.d_esc_list); cudaFree(x.d_esc_count); cudaFree(x.d_gws);
-    cudaFree(x.d_tc_ws); cudaFree(x.d_tc); cudaFree(x.d_tc_v); cudaFree(x.d_tc_off);
+    cudaFree(x.d_tc_ws); cudaFree(x.d_tc); cudaFree(x.d_tc_v); cudaFree(x.d_tc_off); cudaFree(x.d_tc_fb);
     for (int i = 0; i < kNumBuckets; ++i) {
         if (x.side[i]) cudaStreamDestroy(x.side[i]);
         if (x.ev_join[i]) cudaEventDestroy(x.ev_join[i]);
@@ -335,12 +372,13 @@ static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap, size_t tc_total = 0)
     AL(x.d_esc_count, sizeof(int32_t) * 2);
     AL(x.d_gws, 8 * (size_t)h->gws_stride * (size_t)h->gws_grid);
     if (tc_total > 0) {
-        const size_t lists = (size_t)cap * (sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
+        const size_t lists = (size_t)cap * (2 * sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
         x.tc_cap = tc_total - lists;
         AL(x.d_tc_ws, x.tc_cap);
         AL(x.d_tc, sizeof(TcCounters));
         AL(x.d_tc_v, sizeof(int32_t) * (size_t)cap);
         AL(x.d_tc_off, sizeof(int64_t) * (size_t)cap);
+        AL(x.d_tc_fb, sizeof(int32_t) * (size_t)cap);
     }
 #undef AL
     CK(cudaMemset(x.d_esc_count, 0, sizeof(int32_t) * 2));
@@ -469,13 +507,14 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     a.gws = x.d_gws; a.gws_stride = h->gws_stride;
     a.max_points = c.max_points;
     a.nmax_small_f64 = std::min(h->plan[PREC_F64].nmax_smem, c.max_points);
-    if (kind == PREC_FF && x.tc_cap > 0) {
+    if (kind == PREC_FF && x.tc_cap > 0 && h->plan[PREC_FF].tc_nmax > 0) {
         a.tc_ws = x.d_tc_ws;
         a.tc_cap = x.tc_cap;
         a.tc = x.d_tc;
         a.tc_v = x.d_tc_v;
         a.tc_off = x.d_tc_off;
-        a.tc_nmax = std::min(std::min(kTcMaxN, c.max_points), h->plan[PREC_FF].nmax_smem);
+        a.tc_fb = x.d_tc_fb;
+        a.tc_nmax = h->plan[PREC_FF].tc_nmax;
     }
     return a;
 }
@@ -543,9 +582,15 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_count = x.d_bcount + b;
         a.work_next = x.d_next + b;
         a.nmax = B.tri_smem ? B.hi : c.max_points;
-        a.percol_max = B.percol ? B.hi : 0;
-        a.panel = B.panel;
-        CK(launch_solve(kind, B.tri_smem, B.nthr, a, B.grid, B.smem, ss));
+        if (a.tc_ws && B.tcv_ok) {  // the variance goes to the tensor cores
+            a.percol_max = B.v.percol ? B.hi : 0;
+            a.panel = B.v.panel;
+            CK(launch_solve(kind, true, B.v.nthr, a, B.v.grid, B.v.smem, ss, true));
+        } else {
+            a.percol_max = B.percol ? B.hi : 0;
+            a.panel = B.panel;
+            CK(launch_solve(kind, B.tri_smem, B.nthr, a, B.grid, B.smem, ss));
+        }
         ++h->last_launches;
         used |= 1 << (si % kNumBuckets);
     }
@@ -555,6 +600,19 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             CK(cudaStreamWaitEvent(s, x.ev_join[i], 0));
         }
     if (a.tc_ws) {  // variance and Gaussians of the voxels the buckets queued
+        {   // voxels the variant could not hand over (workspace full): regular re-solve
+            SolveArgs f = a;
+            f.tc_ws = nullptr;
+            f.work = a.tc_fb;
+            f.work_base = nullptr;
+            f.work_count = &a.tc->fb_count;
+            f.work_next = &a.tc->fb_next;
+            f.nmax = P.tc_nmax;
+            f.percol_max = default_percol_max(8);
+            f.panel = 16;
+            CK(launch_solve(kind, true, 512, f, P.fb_grid, P.fb_smem, s));
+            ++h->last_launches;
+        }
         CK(launch_var_tc(a, h->sms, s));
         ++h->last_launches;
         if (a.pos) {
@@ -999,10 +1057,15 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
     const int cand[3] = {128, 256, 512};
     for (int b = 0; b < P.nb; ++b) {
         Bucket& B = P.b[b];
+        const bool tcv = a.tc_ws && B.tcv_ok;  // tune the variant the batch entry launches
         float best_ms = 3.0e38f;
-        int best = B.nthr, best_smem = B.smem, best_grid = B.grid;
-        bool best_pc = B.percol;
-        int best_pw = B.panel;
+        int best = tcv ? B.v.nthr : B.nthr, best_smem = tcv ? B.v.smem : B.smem;
+        int best_grid = tcv ? B.v.grid : B.grid;
+        bool best_pc = tcv ? B.v.percol : B.percol;
+        int best_pw = tcv ? B.v.panel : B.panel;
+        const int cur = best;
+        const bool cur_pc = best_pc;
+        const int cur_pw = best_pw;
         for (int ci = 0; ci < 12; ++ci) {
             const int nt = cand[ci % 3];
             const int var = ci / 3;  // blocked with 16-, 8- or 4-column panels, or per column
@@ -1012,10 +1075,10 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
             if (B.tri_smem && nt < B.hi) continue;  // the shared-memory variants need n <= CTA size
             if (!B.tri_smem && nt < 256) continue;
             const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
-                                          tsize(kind), B.tri_smem, nt);
+                                          tsize(kind), B.tri_smem, nt, tcv);
             if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) continue;
             int occ = 0;
-            CK(solve_occupancy(kind, B.tri_smem, nt, sp.total, &occ));
+            CK(solve_occupancy(kind, B.tri_smem, nt, sp.total, &occ, tcv));
             if (occ < 1) continue;
             const int grid = B.tri_smem ? h->sms * occ : h->gws_grid;
             a.work = x.d_work;
@@ -1032,7 +1095,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
                     CK(cudaMemsetAsync(reinterpret_cast<unsigned char*>(a.tc) + 8, 0,
                                        sizeof(TcCounters) - 8, s));
                 CK(cudaEventRecord(e0, s));
-                CK(launch_solve(kind, B.tri_smem, nt, a, grid, sp.total, s));
+                CK(launch_solve(kind, B.tri_smem, nt, a, grid, sp.total, s, tcv));
                 CK(cudaEventRecord(e1, s));
                 CK(cudaEventSynchronize(e1));
                 float t = 0.f;
@@ -1044,12 +1107,14 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
                 best_pw = pw;
             }
         }
-        if (best != B.nthr || best_pc != B.percol || best_pw != B.panel) ++changed;
-        B.percol = best_pc;
-        B.panel = best_pw;
-        B.nthr = best;
-        B.smem = best_smem;
-        B.grid = best_grid;
+        if (best != cur || best_pc != cur_pc || best_pw != cur_pw) ++changed;
+        if (tcv) {
+            B.v.percol = best_pc; B.v.panel = best_pw; B.v.nthr = best; B.v.smem = best_smem;
+            B.v.grid = best_grid;
+        } else {
+            B.percol = best_pc; B.panel = best_pw; B.nthr = best; B.smem = best_smem;
+            B.grid = best_grid;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -32,6 +32,7 @@ constexpr int kNumBuckets = 12; // size buckets of the batched launch
 struct TcCounters {
     unsigned long long total, used;
     int32_t count, next;
+    int32_t fb_count, fb_next;  // voxels the tensor-core solve variant could not hand over
 };
 
 struct SolveArgs {
@@ -84,6 +85,7 @@ struct SolveArgs {
     TcCounters* tc;
     int32_t* tc_v;       // voxels queued for k_var_tc (one entry per voxel at most)
     int64_t* tc_off;     // their byte offsets in tc_ws
+    int32_t* tc_fb;      // voxels re-solved by the regular kernel (workspace full)
     int tc_nmax;         // largest n that takes the tensor-core variance
 };
 
@@ -119,8 +121,10 @@ constexpr int kBigSmem = 216 * 1024;
 
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
+// tcv: the solve variant that hands the variance to k_var_tc (no contraction partials,
+// no staged predictions).
 __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize, bool tri_in_smem,
-                                              int nthr)
+                                              int nthr, bool tcv = false)
 {
     SmemPlan p;
     int nqg = (G * Gp) / kQryBlk;
@@ -139,8 +143,8 @@ __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize
     if (tri_in_smem) o = align16(o + nmax * G * tsize);
     p.off_b = o;
     if (tri_in_smem) o = align16(o + nmax * Gp * tsize);
-    p.off_part = o; o = align16(o + nrg * G * Gp * tsize);
-    p.off_mv = o; o = align16(o + 2 * G * G * 8);
+    p.off_part = o; if (!tcv) o = align16(o + nrg * G * Gp * tsize);
+    p.off_mv = o; if (!tcv) o = align16(o + 2 * G * G * 8);
     p.off_work = o;
     p.pb = 0;
     p.rb = 0;
@@ -176,10 +180,12 @@ inline int default_percol_max(int tsize) { return tsize == 8 ? 96 : 0; }
 cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, int32_t* bcount,
                             int32_t* bbase, int32_t* bcursor, int32_t* work, int32_t* next,
                             int32_t* esc_count, cudaStream_t s);
+// tcv: the float-float shared-memory variant that hands the variance to k_var_tc
 cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& a, int grid, int smem,
-                         cudaStream_t s);
+                         cudaStream_t s, bool tcv = false);
 cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out);
-cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm);
+cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm,
+                            bool tcv = false);
 cudaError_t launch_var_tc(const SolveArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_init_tc(const SolveArgs& a, int sms, cudaStream_t s);
 cudaError_t var_tc_prepare();

@@ -582,7 +582,9 @@ __device__ void big_invert(T* L, int n, T* W, int rbmax)
     __syncthreads();
 }
 
-template <class T, bool TRI_SMEM>
+// TCV: the float-float variant of the tensor-core variance path; it hands every voxel to
+// k_var_tc (or, with the workspace full, to the regular kernel) and carries no contraction.
+template <class T, bool TRI_SMEM, bool TCV>
 __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, const SmemPlan& P,
                             double* red, const T* nodes)
 {
@@ -776,6 +778,11 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         tc = s_tc_off >= 0;
     }
     __syncthreads();
+    if (TCV && !tc) {  // workspace full: the regular kernel re-solves this voxel
+        if (tid == 0) A.tc_fb[atomicAdd(&A.tc->fb_count, 1)] = v;
+        __syncthreads();
+        return;
+    }
 
     // ---- posterior variance at the inputs (per-point noise feedback, Sec. 3.3) -------
     // With A = K + D, k_i = A e_i - d_i e_i gives sf2 - k_i^T A^-1 k_i
@@ -1016,15 +1023,16 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     __syncthreads();
 }
 
-// At most 128 registers per thread at every CTA size, so that 512 threads fit an SM.
-template <class T, bool TRI_SMEM, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs A)
+// At most 128 registers per thread at every CTA size, so that 512 threads fit an SM; the
+// variant without the contraction fits in 85, so that 768 threads do.
+template <class T, bool TRI_SMEM, int NT, bool TCV>
+__global__ void __launch_bounds__(NT, (TCV ? 768 : 512) / NT) k_solve(SolveArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[6 * 32];
     __shared__ T nodes[kMaxG];
     __shared__ int s_v;
-    const SmemPlan P = smem_plan(A.nmax, A.G, A.Gp, (int)sizeof(T), TRI_SMEM, NT);
+    const SmemPlan P = smem_plan(A.nmax, A.G, A.Gp, (int)sizeof(T), TRI_SMEM, NT, TCV);
     // query grid nodes -s/2 + (u + 1/2) s / G, formed once in FP64 and rounded to T
     if (threadIdx.x < A.G)
         nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
@@ -1040,7 +1048,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_solve(SolveArgs A)
         const int v = s_v;
         __syncthreads();
         if (v < 0) break;
-        solve_voxel<T, TRI_SMEM>(A, v, smem, P, red, nodes);
+        solve_voxel<T, TRI_SMEM, TCV>(A, v, smem, P, red, nodes);
     }
 }
 
@@ -1134,20 +1142,21 @@ cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, in
 
 // The dynamic shared-memory limit of every instantiation is raised once, when the
 // handle plans its launches (solve_occupancy), so launches stay capturable.
-template <class T, bool S>
+template <class T, bool S, bool V = false>
 static cudaError_t launch_t(int nthr, const SolveArgs& a, int grid, int smem, cudaStream_t s)
 {
-    if (nthr == 512) k_solve<T, S, 512><<<grid, 512, smem, s>>>(a);
-    else if (nthr == 128) k_solve<T, S, 128><<<grid, 128, smem, s>>>(a);
-    else k_solve<T, S, 256><<<grid, 256, smem, s>>>(a);
+    if (nthr == 512) k_solve<T, S, 512, V><<<grid, 512, smem, s>>>(a);
+    else if (nthr == 128) k_solve<T, S, 128, V><<<grid, 128, smem, s>>>(a);
+    else k_solve<T, S, 256, V><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& a, int grid,
-                         int smem, cudaStream_t s)
+                         int smem, cudaStream_t s, bool tcv)
 {
     if (prec == PREC_F32) return tri_in_smem ? launch_t<float, true>(nthr, a, grid, smem, s) : launch_t<float, false>(nthr, a, grid, smem, s);
     if (prec == PREC_F64) return tri_in_smem ? launch_t<double, true>(nthr, a, grid, smem, s) : launch_t<double, false>(nthr, a, grid, smem, s);
+    if (tcv && tri_in_smem) return launch_t<ff, true, true>(nthr, a, grid, smem, s);
     return tri_in_smem ? launch_t<ff, true>(nthr, a, grid, smem, s) : launch_t<ff, false>(nthr, a, grid, smem, s);
 }
 
@@ -1170,18 +1179,19 @@ cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out)
     return cudaSuccess;
 }
 
-template <class T, bool S>
+template <class T, bool S, bool V = false>
 static const void* kfun(int nthr)
 {
-    return nthr == 512 ? (const void*)k_solve<T, S, 512>
-                       : (nthr == 128 ? (const void*)k_solve<T, S, 128> : (const void*)k_solve<T, S, 256>);
+    return nthr == 512 ? (const void*)k_solve<T, S, 512, V>
+                       : (nthr == 128 ? (const void*)k_solve<T, S, 128, V> : (const void*)k_solve<T, S, 256, V>);
 }
 
-cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm)
+cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm, bool tcv)
 {
     const void* f;
     if (prec == PREC_F32) f = tri_in_smem ? kfun<float, true>(nthr) : kfun<float, false>(nthr);
     else if (prec == PREC_F64) f = tri_in_smem ? kfun<double, true>(nthr) : kfun<double, false>(nthr);
+    else if (tcv && tri_in_smem) f = kfun<ff, true, true>(nthr);
     else f = tri_in_smem ? kfun<ff, true>(nthr) : kfun<ff, false>(nthr);
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
