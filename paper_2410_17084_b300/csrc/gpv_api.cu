@@ -82,6 +82,8 @@ struct SolveCtx {
     int32_t* d_tc_v = nullptr;
     int64_t* d_tc_off = nullptr;
     int32_t* d_tc_fb = nullptr;
+    long long* d_tc_off_v = nullptr;  // per row
+    int32_t* d_tc_next = nullptr;     // k_var_tc dequeue counter per size bucket
     cudaStream_t side[kNumBuckets] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kNumBuckets] = {};
@@ -287,7 +289,8 @@ static size_t tc_bytes(const gp_voxels_config* c, int Gp, size_t rest)
     const int nmax = std::min(kTcMaxN, c->max_points);
     size_t b = std::min((size_t)c->tc_workspace_mb << 20,
                         (size_t)c->max_voxels * (size_t)tc_need_bytes(nmax, c->grid_side, Gp));
-    b += (size_t)c->max_voxels * (2 * sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
+    b += (size_t)c->max_voxels * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
+         sizeof(int32_t) * kNumBuckets;
     if (c->mem_budget) b = c->mem_budget > rest ? std::min(b, c->mem_budget - rest) : 0;
     return b < ((size_t)16 << 20) ? 0 : b;
 }
@@ -322,6 +325,7 @@ static void ctx_release(SolveCtx& x)
     cudaFree(x.d_bcount); cudaFree(x.d_bbase); cudaFree(x.d_bcursor); cudaFree(x.d_next);
     cudaFree(x.d_work); cudaFree(x.d_esc_list); cudaFree(x.d_esc_count); cudaFree(x.d_gws);
     cudaFree(x.d_tc_ws); cudaFree(x.d_tc); cudaFree(x.d_tc_v); cudaFree(x.d_tc_off); cudaFree(x.d_tc_fb);
+    cudaFree(x.d_tc_off_v); cudaFree(x.d_tc_next);
     for (int i = 0; i < kNumBuckets; ++i) {
         if (x.side[i]) cudaStreamDestroy(x.side[i]);
         if (x.ev_join[i]) cudaEventDestroy(x.ev_join[i]);
@@ -372,13 +376,16 @@ static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap, size_t tc_total = 0)
     AL(x.d_esc_count, sizeof(int32_t) * 2);
     AL(x.d_gws, 8 * (size_t)h->gws_stride * (size_t)h->gws_grid);
     if (tc_total > 0) {
-        const size_t lists = (size_t)cap * (2 * sizeof(int32_t) + sizeof(int64_t)) + sizeof(TcCounters);
+        const size_t lists = (size_t)cap * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
+                             sizeof(int32_t) * kNumBuckets;
         x.tc_cap = tc_total - lists;
         AL(x.d_tc_ws, x.tc_cap);
         AL(x.d_tc, sizeof(TcCounters));
         AL(x.d_tc_v, sizeof(int32_t) * (size_t)cap);
         AL(x.d_tc_off, sizeof(int64_t) * (size_t)cap);
         AL(x.d_tc_fb, sizeof(int32_t) * (size_t)cap);
+        AL(x.d_tc_off_v, sizeof(long long) * (size_t)cap);
+        AL(x.d_tc_next, sizeof(int32_t) * kNumBuckets);
     }
 #undef AL
     CK(cudaMemset(x.d_esc_count, 0, sizeof(int32_t) * 2));
@@ -514,6 +521,7 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.tc_v = x.d_tc_v;
         a.tc_off = x.d_tc_off;
         a.tc_fb = x.d_tc_fb;
+        a.tc_off_v = x.d_tc_off_v;
         a.tc_nmax = h->plan[PREC_FF].tc_nmax;
     }
     return a;
@@ -567,6 +575,10 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         return GPV_OK;
     }
 
+    if (a.tc_ws) {  // no row handed over yet; per-bucket dequeue counters of k_var_tc
+        CK(cudaMemsetAsync(a.tc_off_v, 0xFF, sizeof(long long) * (size_t)nvox, s));
+        CK(cudaMemsetAsync(x.d_tc_next, 0, sizeof(int32_t) * kNumBuckets, s));
+    }
     // Batched: one persistent launch per size bucket, buckets on forked streams.
     // Buckets whose factor lives in the global workspace share it, so they run
     // one after another on the first side stream.
@@ -586,6 +598,10 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             a.percol_max = B.v.percol ? B.hi : 0;
             a.panel = B.v.panel;
             CK(launch_solve(kind, true, B.v.nthr, a, B.v.grid, B.v.smem, ss, true));
+            ++h->last_launches;
+            SolveArgs av = a;  // then the bucket's variances, on the same stream
+            av.work_next = x.d_tc_next + b;
+            CK(launch_var_tc(av, h->sms, ss));
         } else {
             a.percol_max = B.percol ? B.hi : 0;
             a.panel = B.panel;
@@ -613,8 +629,6 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             CK(launch_solve(kind, true, 512, f, P.fb_grid, P.fb_smem, s));
             ++h->last_launches;
         }
-        CK(launch_var_tc(a, h->sms, s));
-        ++h->last_launches;
         if (a.pos) {
             CK(launch_init_tc(a, h->sms, s));
             ++h->last_launches;

@@ -86,6 +86,7 @@ struct SolveArgs {
     int32_t* tc_v;       // voxels queued for k_var_tc (one entry per voxel at most)
     int64_t* tc_off;     // their byte offsets in tc_ws
     int32_t* tc_fb;      // voxels re-solved by the regular kernel (workspace full)
+    long long* tc_off_v; // per output row: workspace byte offset, -1 if not handed over
     int tc_nmax;         // largest n that takes the tensor-core variance
 };
 

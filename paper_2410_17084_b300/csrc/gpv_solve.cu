@@ -1005,6 +1005,7 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             const int slot = atomicAdd(&A.tc->count, 1);
             A.tc_v[slot] = v;
             A.tc_off[slot] = s_tc_off;
+            A.tc_off_v[v] = s_tc_off;
         }
         __syncthreads();
         return;

@@ -21,7 +21,9 @@
 // s + t > 5 are dropped (2^-48 as well).  V = L0 + ... + L4 is assembled and squared in
 // float-float.
 //
-// Organisation.  One persistent CTA per SM (256 threads) owns the tensor memory: five
+// Organisation.  Each size bucket launches this kernel on its own stream right after its
+// solve launch, over the same work list, so the variance of small voxels overlaps the
+// factors of large ones.  One persistent CTA per SM (512 threads) owns the tensor memory: five
 // accumulators of 128 lanes (the queries of one M tile) x up to 96 columns (rows j of
 // L^-1 per pass).  For each 16-wide chunk of i, all threads cut the A slices (K*^T: 128
 // queries x 16) and the B slices (L^-1: up to 96 rows x 16) into one of two shared-memory
@@ -174,7 +176,9 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
     __shared__ int s_item, s_next;
     __shared__ int s_broken;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int count = A.tc->count;
+    // the voxels of one size bucket (the solve launch's own work list)
+    const int32_t* work = A.work + (A.work_base ? *A.work_base : 0);
+    const int count = *A.work_count;
     if (count == 0) return;
     ff* nrm2 = reinterpret_cast<ff*>(sm + kOffNrm);
     const int G = A.G, Gp = A.Gp, GG = G * G;
@@ -192,24 +196,32 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
     const uint32_t abase = umma::smem_addr(sm + kOffA), bbase = umma::smem_addr(sm + kOffB);
     uint32_t uses[2] = {0u, 0u};  // commits issued per buffer (identical in every thread)
     int chunk = 0;
-    if (tid == 0) s_item = atomicAdd(&A.tc->next, 1);
+    if (tid == 0) s_item = atomicAdd(A.work_next, 1);
     __syncthreads();
 
     for (;;) {
         const int it = s_item;
         if (it >= count) break;
-        if (tid == 0) s_next = atomicAdd(&A.tc->next, 1);  // one voxel ahead
-        const int v = A.tc_v[it];
+        if (tid == 0) s_next = atomicAdd(A.work_next, 1);  // one voxel ahead
+        const int v = work[it];
+        const long long off = A.tc_off_v[v];
         const int n = (int)(A.offsets[v + 1] - A.offsets[v]);
         const float sf2f = A.sf2[v];
         __syncthreads();
         {   // the next voxel's workspace travels to L2 meanwhile
             const int nx = s_next;
             if (nx < count) {
-                const int vn = A.tc_v[nx];
+                const int vn = work[nx];
+                const long long on = A.tc_off_v[vn];
                 const int nn = (int)(A.offsets[vn + 1] - A.offsets[vn]);
-                prefetch_l2(A.tc_ws + A.tc_off[nx], tc_need_bytes(nn, G, Gp));
+                if (on >= 0) prefetch_l2(A.tc_ws + on, tc_need_bytes(nn, G, Gp));
             }
+        }
+        if (off < 0) {  // not handed over: escalated, not SPD, or re-solved by the regular kernel
+            __syncthreads();
+            if (tid == 0) s_item = s_next;
+            __syncthreads();
+            continue;
         }
         if (s_broken) {
             write_failed(A, v, GG, sf2f);
@@ -219,7 +231,7 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
             continue;
         }
         const int ntri = n * (n + 1) / 2;
-        const ff* X = reinterpret_cast<const ff*>(A.tc_ws + A.tc_off[it]);
+        const ff* X = reinterpret_cast<const ff*>(A.tc_ws + off);
         const ff* FA = X + ntri;
         const ff* FB = FA + n * G;
         const ff* MU = FB + n * Gp;

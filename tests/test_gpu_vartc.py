@@ -89,7 +89,7 @@ def test_tc_quadric_against_oracle_and_cuda_cores(gpv, oracle):
     b = _quadric(600, seed=31)
     tc, l_tc = _run(gpv, b)
     cc, l_cc = _run(gpv, b, tc_workspace_mb=0)
-    assert l_tc == l_cc + 3  # re-solve of what was not handed over (none), k_var_tc, k_init_tc
+    assert l_tc > l_cc + 2  # k_var_tc per bucket, the re-solve of what was not handed over, k_init_tc
     solved = _oracle_check(b, tc, oracle, "tc quadric G=16")
     _agree(b, tc, cc, solved, "tc quadric G=16")
 
@@ -107,7 +107,7 @@ def test_tc_grid_sides(gpv, oracle, shape):
     b = full.subset(idx)
     tc, l_tc = _run(gpv, b)
     cc, l_cc = _run(gpv, b, tc_workspace_mb=0)
-    assert l_tc == l_cc + 3
+    assert l_tc > l_cc + 2
     solved = _oracle_check(b, tc, oracle, f"tc {shape}")
     _agree(b, tc, cc, solved, f"tc {shape}")
 
