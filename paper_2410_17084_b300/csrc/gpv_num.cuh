@@ -194,6 +194,37 @@ __device__ __forceinline__ ff gexp(ff x)
     return ff_make(ldexpf(p.hi, ki), ldexpf(p.lo, ki));
 }
 
+// exp(x) for ff x <= 0 with a table tab[m] = 2^(m/256) (float-float, m = 0..255):
+// x = (256 k + m) ln2/256 + r with |r| <= ln2/512, so exp(x) = 2^k tab[m] exp(r), and exp(r)
+// is its Taylor polynomial of degree 4 (remainder below r^5/120 < 2^-54).  ln2/256 is split
+// as L1 + L2 (floats) + 3.4e-19; n L1 and n L2 are formed exactly (TwoProduct), so the
+// reduction errs by |n| 3.4e-19, below 5e-17 of the result's scale for every x.
+__device__ __forceinline__ ff gexp_tab(ff x, const ff* tab)
+{
+    if (x.hi < -87.0f) return ff_make(0.f, 0.f);
+    const float L1 = 0.0027076061815023422f;
+    const float L2 = -7.440055516116928e-12f;
+    const float nf = rintf(__fmul_rn(x.hi, 369.3299255371094f));  // 256 / ln 2
+    const ff a = two_prod(nf, L1);
+    const ff b = two_prod(nf, L2);
+    const ff r = (x - a) - b;
+    ff p = ff_make(0.0416666679084301f, -1.2417634698280722e-09f);          // 1/24
+    p = p * r + ff_make(0.1666666716337204f, -4.967053879312289e-09f);    // 1/6
+    p = p * r + ff_make(0.5f, 0.f);
+    p = p * r + ff_make(1.f, 0.f);
+    p = p * r + ff_make(1.f, 0.f);
+    const int n = (int)nf;
+    const int k = n >> 8, m = n & 255;  // floor division: n = 256 k + m, 0 <= m < 256
+    const ff t = tab[m] * p;
+    return ff_make(ldexpf(t.hi, k), ldexpf(t.lo, k));
+}
+
+// exp of the working type: float and double by CUDA's own functions, float-float by the
+// table form above
+__device__ __forceinline__ float gexpw(float x, const ff*) { return expf(x); }
+__device__ __forceinline__ double gexpw(double x, const ff*) { return exp(x); }
+__device__ __forceinline__ ff gexpw(ff x, const ff* tab) { return gexp_tab(x, tab); }
+
 // ---- fused multiply-add in the working type -----------------------------------
 // c + a b for ff: exact leading product (TwoProduct), cross terms in FP32, exact sum of
 // the leading parts (TwoSum), one renormalisation.  The error is bounded relative to

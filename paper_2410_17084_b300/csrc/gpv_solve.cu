@@ -586,7 +586,7 @@ __device__ void big_invert(T* L, int n, T* W, int rbmax)
 // k_var_tc (or, with the workspace full, to the regular kernel) and carries no contraction.
 template <class T, bool TRI_SMEM, bool TCV>
 __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, const SmemPlan& P,
-                            double* red, const T* nodes)
+                            double* red, const T* nodes, const ff* xtab)
 {
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -688,8 +688,8 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             }
             const T d1a = x1[re[0]] - x1[ce[0]], d2a = x2[re[0]] - x2[ce[0]];
             const T d1b = x1[re[1]] - x1[ce[1]], d2b = x2[re[1]] - x2[ce[1]];
-            T ka = sf2 * gexp(nlam * (d1a * d1a + d2a * d2a));
-            T kb = sf2 * gexp(nlam * (d1b * d1b + d2b * d2b));
+            T ka = sf2 * gexpw(nlam * (d1a * d1a + d2a * d2a), xtab);
+            T kb = sf2 * gexpw(nlam * (d1b * d1b + d2b * d2b), xtab);
             if (re[0] == ce[0]) ka = ka + (A.noise ? from_f<T>(__ldg(A.noise + beg + re[0])) : sn2);
             if (re[1] == ce[1]) kb = kb + (A.noise ? from_f<T>(__ldg(A.noise + beg + re[1])) : sn2);
             L[e0] = ka;
@@ -826,8 +826,8 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             const int i0 = t0 / G, u0 = t0 - i0 * G, i1 = t1 / G, u1 = t1 - i1 * G;
             const T da0 = x1[i0] - nodes[u0], db0 = x2[i0] - nodes[u0];
             const T da1 = x1[i1] - nodes[u1], db1 = x2[i1] - nodes[u1];
-            const T ea0 = gexp(nlam * (da0 * da0)), eb0 = gexp(nlam * (db0 * db0));
-            const T ea1 = gexp(nlam * (da1 * da1)), eb1 = gexp(nlam * (db1 * db1));
+            const T ea0 = gexpw(nlam * (da0 * da0), xtab), eb0 = gexpw(nlam * (db0 * db0), xtab);
+            const T ea1 = gexpw(nlam * (da1 * da1), xtab), eb1 = gexpw(nlam * (db1 * db1), xtab);
             fa[i0 * G + u0] = sf2 * ea0;
             fb[i0 * Gp + u0] = eb0;
             if (t0 + nthr < n * G) {
@@ -842,12 +842,12 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     } else {
         const T dl = from_d<T>((double)A.size / (double)G);
         const T two = from_f<T>(2.f);
-        const T cst = gexp(nlam * (dl * dl) * two);  // exp(-2 lambda delta^2)
+        const T cst = gexpw(nlam * (dl * dl) * two, xtab);  // exp(-2 lambda delta^2)
         for (int t = tid; t < 2 * n; t += nthr) {
             const int i = t >> 1;
             const T d0 = ((t & 1) ? x2[i] : x1[i]) - nodes[0];  // x - u_0
-            T e = gexp(nlam * (d0 * d0));
-            T r = gexp(nlam * (dl * dl - two * dl * d0));
+            T e = gexpw(nlam * (d0 * d0), xtab);
+            T r = gexpw(nlam * (dl * dl - two * dl * d0), xtab);
             if ((t & 1) == 0) {
                 for (int k = 0; k < G; ++k) {
                     fa[i * G + k] = sf2 * e;
@@ -1032,12 +1032,19 @@ __global__ void __launch_bounds__(NT, (TCV ? 768 : 512) / NT) k_solve(SolveArgs 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[6 * 32];
     __shared__ T nodes[kMaxG];
+    __shared__ ff xtab[is_ff<T>::value ? 256 : 1];  // 2^(m/256) for the float-float exp
     __shared__ int s_v;
     const SmemPlan P = smem_plan(A.nmax, A.G, A.Gp, (int)sizeof(T), TRI_SMEM, NT, TCV);
     // query grid nodes -s/2 + (u + 1/2) s / G, formed once in FP64 and rounded to T
     if (threadIdx.x < A.G)
         nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
                                        ((double)threadIdx.x + 0.5) * (double)A.size / (double)A.G);
+    if (is_ff<T>::value)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+            const double t = exp2((double)i / 256.0);
+            const float h = (float)t;
+            xtab[i] = ff_make(h, (float)(t - (double)h));
+        }
     const int total = *A.work_count;
     const int base = A.work_base ? *A.work_base : 0;
     for (;;) {
@@ -1049,7 +1056,7 @@ __global__ void __launch_bounds__(NT, (TCV ? 768 : 512) / NT) k_solve(SolveArgs 
         const int v = s_v;
         __syncthreads();
         if (v < 0) break;
-        solve_voxel<T, TRI_SMEM, TCV>(A, v, smem, P, red, nodes);
+        solve_voxel<T, TRI_SMEM, TCV>(A, v, smem, P, red, nodes, xtab);
     }
 }
 
@@ -1170,7 +1177,7 @@ cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const int static_bytes = 6 * 32 * 8 + 32 * 8 + 64;
+    const int static_bytes = 6 * 32 * 8 + 32 * 8 + 64 + 256 * 8;
     int best = 0;
     for (int n = 8; n <= 1024; n += 8) {
         SmemPlan p = smem_plan(n, G, Gp, tsize_of(prec), true, solve_threads(n, true));
