@@ -146,3 +146,22 @@ def test_tc_repeatable(gpv):
     c, _ = _run(gpv, b)
     for k in ("mean", "var", "status", "pos", "scale", "quat"):
         assert np.array_equal(a[k], c[k]), k
+
+
+def test_tc_workspace_within_memory_budget(gpv, oracle):
+    """Under mem_budget the workspace takes what the budget leaves (here about 64 MB): a
+    batch that fits takes the tensor-core variance, and the handle stays within budget."""
+    b = _quadric(300, seed=38)
+    # room for 5,000 voxels: the budget, not max_voxels, bounds the workspace
+    base = dict(voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau,
+                max_points=int(b.counts.max()), max_voxels=5000, precision=1, mean_mode=1)
+    rest = gpv.gp_voxels_query_sizes(gpv.gp_voxels_config_default(tc_workspace_mb=0, **base))
+    budget = rest + (64 << 20)
+    unbounded = gpv.gp_voxels_query_sizes(gpv.gp_voxels_config_default(**base))
+    assert unbounded > budget
+    assert gpv.gp_voxels_query_sizes(gpv.gp_voxels_config_default(mem_budget=budget, **base)) <= budget
+    tc, l_tc = _run(gpv, b, mem_budget=budget, max_voxels=5000)
+    cc, l_cc = _run(gpv, b, tc_workspace_mb=0, max_voxels=5000)
+    assert l_tc > l_cc + 2  # the tensor-core variance ran
+    solved = _oracle_check(b, tc, oracle, "tc under a memory budget")
+    _agree(b, tc, cc, solved, "tc under a memory budget")
