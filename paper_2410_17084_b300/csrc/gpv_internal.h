@@ -140,10 +140,20 @@ __host__ __device__ inline SmemPlan smem_plan(int nmax, int G, int Gp, int tsize
     if (tri_in_smem) o = align16(o + (int)(((int64_t)nmax * (nmax + 1) / 2 + 16) * tsize));
     // the cross-covariance factors live next to the triangle: in shared memory, or in
     // the CTA's slice of the global workspace
-    p.off_a = o;
-    if (tri_in_smem) o = align16(o + nmax * G * tsize);
-    p.off_b = o;
-    if (tri_in_smem) o = align16(o + nmax * Gp * tsize);
+    // the variant without the contraction forms the factors after L^-1 has been handed
+    // over, so where they fit they lie over the triangle
+    const int64_t tri_bytes = ((int64_t)nmax * (nmax + 1) / 2 + 16) * tsize;
+    const bool overlay = tcv && tri_in_smem &&
+                         (int64_t)align16(nmax * G * tsize) + (int64_t)nmax * Gp * tsize <= tri_bytes;
+    if (overlay) {
+        p.off_a = p.off_tri;
+        p.off_b = p.off_tri + align16(nmax * G * tsize);
+    } else {
+        p.off_a = o;
+        if (tri_in_smem) o = align16(o + nmax * G * tsize);
+        p.off_b = o;
+        if (tri_in_smem) o = align16(o + nmax * Gp * tsize);
+    }
     p.off_part = o; if (!tcv) o = align16(o + nrg * G * Gp * tsize);
     p.off_mv = o; if (!tcv) o = align16(o + 2 * G * G * 8);
     p.off_work = o;

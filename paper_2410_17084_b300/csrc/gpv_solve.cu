@@ -820,53 +820,58 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     // r_{k+1} = r_k exp(-2 lambda delta^2): three exponentials per point and axis (and one
     // per voxel) instead of G, the rest products whose rounding grows only linearly in k
     // (in the 8-byte types; FP32 evaluates every exponential, its variance has no margin)
-    if (sizeof(T) == 4) {
-        for (int t0 = tid; t0 < n * G; t0 += 2 * nthr) {  // four exponentials in flight
-            const int t1 = min(t0 + nthr, n * G - 1);
-            const int i0 = t0 / G, u0 = t0 - i0 * G, i1 = t1 / G, u1 = t1 - i1 * G;
-            const T da0 = x1[i0] - nodes[u0], db0 = x2[i0] - nodes[u0];
-            const T da1 = x1[i1] - nodes[u1], db1 = x2[i1] - nodes[u1];
-            const T ea0 = gexpw(nlam * (da0 * da0), xtab), eb0 = gexpw(nlam * (db0 * db0), xtab);
-            const T ea1 = gexpw(nlam * (da1 * da1), xtab), eb1 = gexpw(nlam * (db1 * db1), xtab);
-            fa[i0 * G + u0] = sf2 * ea0;
-            fb[i0 * Gp + u0] = eb0;
-            if (t0 + nthr < n * G) {
-                fa[i1 * G + u1] = sf2 * ea1;
-                fb[i1 * Gp + u1] = eb1;
-            }
-        }
-        for (int t = tid; t < n * (Gp - G); t += nthr) {
-            const int i = t / (Gp - G), u = G + (t - i * (Gp - G));
-            fb[i * Gp + u] = zero<T>();
-        }
-    } else {
-        const T dl = from_d<T>((double)A.size / (double)G);
-        const T two = from_f<T>(2.f);
-        const T cst = gexpw(nlam * (dl * dl) * two, xtab);  // exp(-2 lambda delta^2)
-        for (int t = tid; t < 2 * n; t += nthr) {
-            const int i = t >> 1;
-            const T d0 = ((t & 1) ? x2[i] : x1[i]) - nodes[0];  // x - u_0
-            T e = gexpw(nlam * (d0 * d0), xtab);
-            T r = gexpw(nlam * (dl * dl - two * dl * d0), xtab);
-            if ((t & 1) == 0) {
-                for (int k = 0; k < G; ++k) {
-                    fa[i * G + k] = sf2 * e;
-                    e = e * r;
-                    r = r * cst;
-                }
-            } else {
-                for (int k = 0; k < G; ++k) {
-                    fb[i * Gp + k] = e;
-                    e = e * r;
-                    r = r * cst;
+    // (the variant without the contraction forms them after L^-1 has left shared memory:
+    // its smem plan may lay them over the triangle)
+    auto kfactors = [&]() {
+        if (sizeof(T) == 4) {
+            for (int t0 = tid; t0 < n * G; t0 += 2 * nthr) {  // four exponentials in flight
+                const int t1 = min(t0 + nthr, n * G - 1);
+                const int i0 = t0 / G, u0 = t0 - i0 * G, i1 = t1 / G, u1 = t1 - i1 * G;
+                const T da0 = x1[i0] - nodes[u0], db0 = x2[i0] - nodes[u0];
+                const T da1 = x1[i1] - nodes[u1], db1 = x2[i1] - nodes[u1];
+                const T ea0 = gexpw(nlam * (da0 * da0), xtab), eb0 = gexpw(nlam * (db0 * db0), xtab);
+                const T ea1 = gexpw(nlam * (da1 * da1), xtab), eb1 = gexpw(nlam * (db1 * db1), xtab);
+                fa[i0 * G + u0] = sf2 * ea0;
+                fb[i0 * Gp + u0] = eb0;
+                if (t0 + nthr < n * G) {
+                    fa[i1 * G + u1] = sf2 * ea1;
+                    fb[i1 * Gp + u1] = eb1;
                 }
             }
+            for (int t = tid; t < n * (Gp - G); t += nthr) {
+                const int i = t / (Gp - G), u = G + (t - i * (Gp - G));
+                fb[i * Gp + u] = zero<T>();
+            }
+        } else {
+            const T dl = from_d<T>((double)A.size / (double)G);
+            const T two = from_f<T>(2.f);
+            const T cst = gexpw(nlam * (dl * dl) * two, xtab);  // exp(-2 lambda delta^2)
+            for (int t = tid; t < 2 * n; t += nthr) {
+                const int i = t >> 1;
+                const T d0 = ((t & 1) ? x2[i] : x1[i]) - nodes[0];  // x - u_0
+                T e = gexpw(nlam * (d0 * d0), xtab);
+                T r = gexpw(nlam * (dl * dl - two * dl * d0), xtab);
+                if ((t & 1) == 0) {
+                    for (int k = 0; k < G; ++k) {
+                        fa[i * G + k] = sf2 * e;
+                        e = e * r;
+                        r = r * cst;
+                    }
+                } else {
+                    for (int k = 0; k < G; ++k) {
+                        fb[i * Gp + k] = e;
+                        e = e * r;
+                        r = r * cst;
+                    }
+                }
+            }
+            for (int t = tid; t < n * (Gp - G); t += nthr) {
+                const int i = t / (Gp - G), u = G + (t - i * (Gp - G));
+                fb[i * Gp + u] = zero<T>();
+            }
         }
-        for (int t = tid; t < n * (Gp - G); t += nthr) {
-            const int i = t / (Gp - G), u = G + (t - i * (Gp - G));
-            fb[i * Gp + u] = zero<T>();
-        }
-    }
+    };
+    if (!TCV) kfactors();
     __syncthreads();
     for (int i = tid; i < n; i += nthr) {  // four partial sums in flight
         T s4[4] = {zero<T>(), zero<T>(), zero<T>(), zero<T>()};
@@ -885,8 +890,6 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     T* Wtc = tc ? reinterpret_cast<T*>(A.tc_ws + s_tc_off) : nullptr;
     if (tc) {
         for (int e = tid; e < ntri; e += nthr) Wtc[e] = L[e];
-        for (int e = tid; e < n * G; e += nthr) Wtc[ntri + e] = fa[e];
-        for (int e = tid; e < n * Gp; e += nthr) Wtc[ntri + n * G + e] = fb[e];
         // slice exponents: rows j of L^-1 and queries (u, v) of K* = a(u) b(v)
         int* EX = reinterpret_cast<int*>(Wtc + ntri + n * G + n * Gp + 2 * GG);
         for (int j = tid; j < n; j += nthr) {
@@ -894,6 +897,13 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             for (int i = 0; i <= j; ++i) mx = fmaxf(mx, fabsf(hi_of(L[tri_off(i, n) + j - i])));
             EX[j] = tc_exp_above(mx);
         }
+        if (TCV) {  // L^-1 is in the workspace: now the factors
+            __syncthreads();
+            kfactors();
+            __syncthreads();
+        }
+        for (int e = tid; e < n * G; e += nthr) Wtc[ntri + e] = fa[e];
+        for (int e = tid; e < n * Gp; e += nthr) Wtc[ntri + n * G + e] = fb[e];
         for (int q = tid; q < GG; q += nthr) {
             const int u = q / G, vq = q - u * G;
             float mx = 0.f;
