@@ -117,7 +117,7 @@ typedef struct {
                             voxel; gp_voxels_autotune may choose otherwise per size bucket */
     int tc_workspace_mb; /* GPV_PREC_MIXED batch solves: MiB of device workspace for the
                             posterior variance on the tensor cores (Eq. 3, diag(Sigma*) by
-                            exact BF16 slice products; voxels of up to 160 points whose factor
+                            exact BF16 slice products; voxels of up to 192 points whose factor
                             fits shared memory).  A call whose eligible voxels need more than
                             this forms every variance on the CUDA cores instead, so the
                             choice never depends on scheduling.  0 turns it off; default

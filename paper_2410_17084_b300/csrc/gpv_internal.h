@@ -90,9 +90,17 @@ struct SolveArgs {
     int tc_nmax;         // largest n that takes the tensor-core variance
 };
 
-// Largest n of the tensor-core variance: with 8-bit slices the FP32 sums of the four
-// exact accumulator levels stay below 2^24 grid units for n <= 170.
-constexpr int kTcMaxN = 160;
+// Conditioning limit of the tensor-core variance: voxels whose pivot ratio
+// (max L_ii / min L_ii)^2 exceeds it keep the float-float contraction on the CUDA cores.
+// The slices share one exponent per row of L^-1 and per query, so entries far below their
+// row's largest carry fewer bits than in float-float; the worst voxels of the workloads
+// stay under 1e4, the 1e5 limit leaves a factor of ten.
+constexpr float kTcCond = 1e5f;
+
+// Largest n of the tensor-core variance: with 8-bit slices of at most 2^7 grid units the FP32
+// sums of the four exact accumulator levels stay below 2^24 units for n < 256 (level 3:
+// 4 x 2^14 n); 192 is the largest shared-memory size bucket.
+constexpr int kTcMaxN = 192;
 
 // Workspace bytes of one voxel: packed L^-1, the factors (n G and n Gp), the G^2 means
 // and the G^2 variances, float-float, then the slice exponents of the n rows of L^-1 and

@@ -265,15 +265,16 @@ __device__ __forceinline__ ff acc_norm(ff a) { return fast_two_sum(a.hi, a.lo); 
 
 template <class T> __device__ __forceinline__ T zero() { return from_f<T>(0.f); }
 
-// Slice exponent of the tensor-core variance: the smallest E with m < 2^E for the largest
-// magnitude m of a row (leading parts; the margin covers their rounding), kept where the
-// slice grids 2^(E-8) .. 2^(E-48) stay normal FP32 numbers.
+// Slice exponent of the tensor-core variance: E with m < 2^(E-1) for the largest magnitude
+// m of a row (leading parts; the margin covers their rounding), so the first 8-bit slice
+// of every entry holds at most 7 bits (|slice| <= 2^7 grid units, like the later ones);
+// kept where the slice grids 2^(E-8) .. 2^(E-48) stay normal FP32 numbers.
 __device__ __forceinline__ int tc_exp_above(float m)
 {
     if (!(m > 0.f)) return -100;
     int e;
     frexpf(m * 1.000001f, &e);
-    return max(-100, min(100, e));
+    return max(-100, min(100, e + 1));
 }
 
 template <class T> struct is_ff { static constexpr bool value = false; };

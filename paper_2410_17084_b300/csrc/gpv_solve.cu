@@ -768,7 +768,7 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         if (tid == 0) {
             long long off = -1;
             const unsigned long long need = tc_need_bytes(n, G, Gp);
-            if (A.tc->total <= A.tc_cap) {
+            if (A.tc->total <= A.tc_cap && !(dmax > kTcCond * dmin)) {
                 const unsigned long long o = atomicAdd(&A.tc->used, need);
                 if (o + need <= A.tc_cap) off = (long long)o;
             }

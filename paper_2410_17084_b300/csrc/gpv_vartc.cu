@@ -8,24 +8,28 @@
 // so V needs some 48 significant bits, more than any single tensor-core product
 // carries.  The error-free splitting of Ozaki, Ogita, Oishi and Rump (Numer. Algorithms
 // 59, 2012) gets them from BF16 products: every entry is cut into six slices of 8 bits on
-// a power-of-two grid shared by its row (row j of L^-1: 2^E_j > max_i |L^-1_ji|; the
-// column of query q in K*: 2^F_q > max_i |k_iq|).  Slice s of an entry is a multiple of
-// 2^(E - 8(s+1)) with at most 8 significant bits, so it is exactly a BF16 number, and a
-// product of two slices is exact in FP32.  All products of one level l = s + t lie on one
-// grid, and for l <= 3 the sum of their magnitudes over the pairs of the level and over
-// i stays below 2^24 grid units when n <= 160 (level 3: 6 * 2^14 n), so the tensor core's
-// FP32 accumulation of each of these levels is exact.  Levels 4 and 5 share a fifth
-// accumulator; its values stay near 2^-29 of 2^(E_j + F_q), so its FP32 rounding lies
-// about 2^-48 below that scale.  (A level's sum is not small: it reaches 2^19 of its own
-// grid, which is why level 3 needs an exact accumulator of its own.)  Pairs with
-// s + t > 5 are dropped (2^-48 as well).  V = L0 + ... + L4 is assembled and squared in
-// float-float.
+// a power-of-two grid shared by its row (row j of L^-1: 2^(E_j - 1) > max_i |L^-1_ji|; the
+// column of query q in K*: 2^(F_q - 1) > max_i |k_iq|).  Slice s of an entry is a multiple
+// of 2^(E - 8(s+1)) of at most 2^7 grid units, so it is exactly a BF16 number, and a
+// product of two slices is exact in FP32 (at most 2^14 units).  All products of one level
+// l = s + t lie on one grid, and for l <= 4 the sum of their magnitudes over the pairs of
+// the level and over i stays below 2^24 grid units when n < 204 (level 4: 5 * 2^14 n), so
+// the tensor core's FP32 accumulation of each of these levels is exact.  Level 5 has an
+// accumulator of its own too, inexact: its values stay near 2^-32 of 2^(E_j + F_q), its
+// FP32 rounding far below 2^-48 of that scale.  (A level's sum is not small: it reaches
+// 2^19 of its own grid, which is why every level down to 4 needs an exact accumulator.)
+// Pairs with s + t > 5 are dropped (2^-48).  V = L0 + ... + L5 is assembled and squared
+// in float-float.
+//
+// Up to 160 points levels 4 and 5 share the fifth accumulator (its rounding stays near 2^-48
+// of the row scale at that size) and a pass takes 96 rows of L^-1; above, six accumulators
+// of 80 columns.
 //
 // Organisation.  Each size bucket launches this kernel on its own stream right after its
 // solve launch, over the same work list, so the variance of small voxels overlaps the
-// factors of large ones.  One persistent CTA per SM (512 threads) owns the tensor memory: five
-// accumulators of 128 lanes (the queries of one M tile) x up to 96 columns (rows j of
-// L^-1 per pass).  For each 16-wide chunk of i, all threads cut the A slices (K*^T: 128
+// factors of large ones.  One persistent CTA per SM (512 threads) owns the tensor memory:
+// five or six accumulators of 128 lanes (the queries of one M tile) x up to 96 or 80
+// columns (rows j of L^-1 per pass).  For each 16-wide chunk of i, all threads cut the A slices (K*^T: 128
 // queries x 16) and the B slices (L^-1: up to 96 rows x 16) into one of two shared-memory
 // buffers while the tensor core works on the other; one thread issues the 21 MMAs
 // (kind::f16, M = 128, N = rows of the pass, K = 16) and commits them to the buffer's
@@ -45,9 +49,11 @@ namespace {
 
 constexpr int kVT = 512;      // threads per CTA
 constexpr int kSl = 6;        // slices per operand entry
-constexpr int kLv = 5;        // accumulators: levels 0, 1, 2, 3 and 4..5
+constexpr int kLv = 6;        // accumulators: levels 0 .. 5 (n > kLv5MaxN), else 0 .. 3 and 4..5
 constexpr int kMT = 128;      // queries per M tile (tensor-memory lanes)
-constexpr int kNJ = 96;       // rows of L^-1 per pass (MMA N; kLv * kNJ <= 512 columns)
+constexpr int kNJ = 80;       // rows of L^-1 per pass with six accumulators (6 * 80 <= 512)
+constexpr int kNJ5 = 96;      // with five accumulators (5 * 96 <= 512)
+constexpr int kLv5MaxN = 160; // up to here levels 4 and 5 share an accumulator
 constexpr int kKC = 16;       // K of one MMA (BF16)
 constexpr int kSliceBytes = 128 * kKC * 2;  // one slice of a 128 x 16 operand chunk
 constexpr int kParts = kVT / kMT;             // threads per operand row (K chunk split)
@@ -65,7 +71,7 @@ constexpr int kVarTcSmem = kOffEnd > 120 * 1024 ? kOffEnd : 120 * 1024;
 
 __device__ __forceinline__ int tri_off_p(int c, int n) { return c * n - ((c * (c - 1)) >> 1); }
 
-// Cut x = hi + lo (|x| < 2^E) into kSl slices on the grids 2^(E-8), ..., 2^(E-48):
+// Cut x = hi + lo (|x| < 2^(E-1)) into kSl slices on the grids 2^(E-8), ..., 2^(E-48):
 // round to the grid by adding and subtracting 1.5 * 2^(grid exponent + 23), keep the
 // exact remainder.  The first three slices come from hi alone; lo joins the remainder
 // for the last three (that FP32 sum errs by at most 2^(E-49)).  Returns the FP32 bit
@@ -143,14 +149,16 @@ __device__ __forceinline__ void prefetch_l2(const unsigned char* p, uint64_t byt
         asm volatile("prefetch.global.L2 [%0];" :: "l"(p + o));
 }
 
-// nrm += V^2 with V = l0 + ... + l4 (the levels of one entry of L^-1 K*): the exact levels
-// join the leading part by TwoSum, their errors and the merged tail the trailing part
-__device__ __forceinline__ void acc_levels(ff& nrm, float l0, float l1, float l2, float l3, float l4)
+// nrm += V^2 with V = l0 + ... + l5 (the levels of one entry of L^-1 K*): the exact levels
+// join the leading part by TwoSum, their errors and the last level the trailing part
+__device__ __forceinline__ void acc_levels(ff& nrm, float l0, float l1, float l2, float l3, float l4,
+                                           float l5)
 {
     const ff a = two_sum(l0, l1);
     const ff b = two_sum(a.hi, l2);
     const ff c = two_sum(b.hi, l3);
-    const ff V = ff_make(c.hi, __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), c.lo), l4));
+    const ff d = two_sum(c.hi, l4);
+    const ff V = ff_make(d.hi, __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), __fadd_rn(c.lo, d.lo)), l5));
     acc_fma(nrm, V, V);
 }
 
@@ -240,14 +248,18 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
         const int* FQ = EX + n;                                  // L^-1, then the queries
         bool failed = false;
         const int r = tid & (kMT - 1), h = tid >> 7;  // operand row, part of the K chunk
+        // up to kLv5MaxN points levels 4 and 5 share an accumulator (their FP32 rounding stays
+        // near 2^-48 of the row scale) and a pass takes 96 rows; above, level 4 is exact too
+        const int nlv = n > kLv5MaxN ? kLv : kLv - 1;
+        const int njp = n > kLv5MaxN ? kNJ : kNJ5;
         for (int mt = 0; mt * kMT < GG && !failed; ++mt) {
             const int q = mt * kMT + r;
             const bool qv = q < GG;
             const int u = qv ? q / G : 0, w = qv ? q - u * G : 0;
             const int F = qv ? FQ[q] : 0;
             ff nrm = zero<ff>();
-            for (int j0 = 0; j0 < n && !failed; j0 += kNJ) {
-                const int nj = min(kNJ, n - j0), Np = (nj + 15) & ~15;
+            for (int j0 = 0; j0 < n && !failed; j0 += njp) {
+                const int nj = min(njp, n - j0), Np = (nj + 15) & ~15;
                 const int nkc = (min(n, j0 + nj) + kKC - 1) / kKC;  // rows j < j0 + nj need i <= j
                 const int j = j0 + r;
                 const int Ej = j < n ? EX[j] : 0;
@@ -296,10 +308,10 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                         for (int s = 0; s < kSl; ++s)
 #pragma unroll
                             for (int t = 0; s + t < kSl; ++t) {
-                                const int lv = min(s + t, kLv - 1);
+                                const int lv = min(s + t, nlv - 1);
                                 const bool acc = (started >> lv) & 1u;
                                 started |= 1u << lv;
-                                umma::mma_bf16(tmem + lv * kNJ, umma::make_desc(a0 + t * kSliceBytes, 128, 256),
+                                umma::mma_bf16(tmem + lv * njp, umma::make_desc(a0 + t * kSliceBytes, 128, 256),
                                                umma::make_desc(b0 + s * kSliceBytes, 128, 256), idesc, acc);
                             }
                         umma::mma_commit(&mbar[b]);
@@ -321,8 +333,14 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                     for (int uu = grp; uu < U; uu += kParts) {
                         uint32_t l[kLv][8];
 #pragma unroll
-                        for (int lv = 0; lv < kLv; ++lv)
-                            tmem_ld8_nowait(tmem + lane_base + lv * kNJ + uu * 8, l[lv]);
+                        for (int lv = 0; lv < kLv; ++lv) {
+                            if (lv < nlv) {
+                                tmem_ld8_nowait(tmem + lane_base + lv * njp + uu * 8, l[lv]);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 8; ++c) l[lv][c] = 0u;
+                            }
+                        }
                         tmem_wait_ld();
 #pragma unroll
                         for (int lv = 0; lv < kLv; ++lv) reg_fence8(l[lv]);
@@ -331,7 +349,7 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                             if (j0 + uu * 8 + c < n)
                                 acc_levels(nrm, __uint_as_float(l[0][c]), __uint_as_float(l[1][c]),
                                            __uint_as_float(l[2][c]), __uint_as_float(l[3][c]),
-                                           __uint_as_float(l[4][c]));
+                                           __uint_as_float(l[4][c]), __uint_as_float(l[5][c]));
                     }
                 }
                 umma::fence_before_sync();

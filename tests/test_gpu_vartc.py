@@ -85,7 +85,7 @@ def _quadric(nvox, seed, lo=16, hi=192, pool=None):
 
 def test_tc_quadric_against_oracle_and_cuda_cores(gpv, oracle):
     """16 x 16 grid (two M tiles of 128 queries), counts 16..192 (one or two passes of
-    96 rows of L^-1 up to 160 points, CUDA-core variance above), fused Gaussian init."""
+    96 rows of L^-1), fused Gaussian init."""
     b = _quadric(600, seed=31)
     tc, l_tc = _run(gpv, b)
     cc, l_cc = _run(gpv, b, tc_workspace_mb=0)
@@ -113,14 +113,14 @@ def test_tc_grid_sides(gpv, oracle, shape):
 
 
 def test_tc_largest_eligible_voxels(gpv, oracle):
-    """n = 150..160 (the largest n of the tensor-core variance), next to n just above it
-    (161..170: CUDA-core variance in the same call)."""
-    b = _quadric(120, seed=35, lo=150, hi=170, pool=10000)
-    assert (b.counts > 160).any() and (b.counts <= 160).any()
+    """n = 180..192 (the largest n of the tensor-core variance), next to n just above it
+    (193..200: CUDA-core variance in the same call, factor in the global workspace)."""
+    b = _quadric(120, seed=35, lo=180, hi=200, pool=20000)
+    assert (b.counts > 192).any() and (b.counts <= 192).any()
     tc, _ = _run(gpv, b, max_points=256)
     cc, _ = _run(gpv, b, max_points=256, tc_workspace_mb=0)
-    solved = _oracle_check(b, tc, oracle, "tc n 150..170")
-    _agree(b, tc, cc, solved, "tc n 150..170")
+    solved = _oracle_check(b, tc, oracle, "tc n 180..200")
+    _agree(b, tc, cc, solved, "tc n 180..200")
 
 
 def test_tc_workspace_too_small_falls_back_whole_call(gpv):
