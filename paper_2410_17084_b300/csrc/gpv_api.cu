@@ -60,6 +60,7 @@ struct PrecPlan {
     int* d_hi = nullptr;  // device copy of the bucket upper bounds
     int nmax_smem = 0;
     int tc_nmax = 0;      // largest n of the tensor-core variance (0: off)
+    int tc_nmax_gl = 0;   // the same for the global-workspace buckets
     int fb_smem = 0, fb_grid = 0;  // regular re-solve of what the variant could not hand over
 };
 
@@ -217,8 +218,10 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
     // tensor-core variance (batch entry, float-float): the variant without the contraction
     // for every shared-memory bucket up to its largest n
     P.tc_nmax = 0;
+    P.tc_nmax_gl = 0;
     if (kind == PREC_FF && h->main.tc_cap > 0) {
         P.tc_nmax = std::min(std::min(kTcMaxN, c.max_points), P.nmax_smem);
+        P.tc_nmax_gl = std::min(kTcMaxNGl, c.max_points);
         for (int i = 0; i < P.nb; ++i) {
             Bucket& B = P.b[i];
             if (!B.tri_smem || B.hi > P.tc_nmax) continue;
@@ -523,6 +526,7 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.tc_fb = x.d_tc_fb;
         a.tc_off_v = x.d_tc_off_v;
         a.tc_nmax = h->plan[PREC_FF].tc_nmax;
+        a.tc_nmax_gl = h->plan[PREC_FF].tc_nmax_gl;
     }
     return a;
 }
@@ -606,6 +610,13 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             a.percol_max = B.percol ? B.hi : 0;
             a.panel = B.panel;
             CK(launch_solve(kind, B.tri_smem, B.nthr, a, B.grid, B.smem, ss));
+            if (a.tc_ws && !B.tri_smem && P.tc_nmax_gl > P.nmax_smem) {
+                // workspace voxels hand their variance over as well
+                ++h->last_launches;
+                SolveArgs av = a;
+                av.work_next = x.d_tc_next + b;
+                CK(launch_var_tc(av, h->sms, ss));
+            }
         }
         ++h->last_launches;
         used |= 1 << (si % kNumBuckets);

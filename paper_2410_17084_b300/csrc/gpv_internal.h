@@ -87,7 +87,8 @@ struct SolveArgs {
     int64_t* tc_off;     // their byte offsets in tc_ws
     int32_t* tc_fb;      // voxels re-solved by the regular kernel (workspace full)
     long long* tc_off_v; // per output row: workspace byte offset, -1 if not handed over
-    int tc_nmax;         // largest n that takes the tensor-core variance
+    int tc_nmax;         // largest n that takes the tensor-core variance (factor in shared memory)
+    int tc_nmax_gl;      // the same for voxels whose factor lives in the global workspace
 };
 
 // Conditioning limit of the tensor-core variance: voxels whose pivot ratio
@@ -96,6 +97,13 @@ struct SolveArgs {
 // row's largest carry fewer bits than in float-float; the worst voxels of the workloads
 // stay under 1e4, the 1e5 limit leaves a factor of ten.
 constexpr float kTcCond = 1e5f;
+
+// Largest n of the tensor-core variance for voxels whose factor lives in the global
+// workspace: the four exact levels 0-3 stay exact for n < 256 (4 x 2^14 n); level 4 is
+// exact by the worst-case bound only to n < 204, above that its sum would have to gather
+// 5 n products of up to 2^14 units with one sign (the low slices are close to uniformly
+// distributed, their sums stay near 2^18 units) to round.
+constexpr int kTcMaxNGl = 255;
 
 // Largest n of the tensor-core variance: with 8-bit slices of at most 2^7 grid units the FP32
 // sums of the four exact accumulator levels stay below 2^24 units for n < 256 (level 3:

@@ -764,7 +764,7 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     // ---- tensor-core variance: reserve this voxel's workspace (float-float only) ------
     __shared__ long long s_tc_off;
     bool tc = false;
-    if (is_ff<T>::value && TRI_SMEM && A.tc_ws != nullptr && n <= A.tc_nmax) {
+    if (is_ff<T>::value && A.tc_ws != nullptr && n <= (TRI_SMEM ? A.tc_nmax : A.tc_nmax_gl)) {
         if (tid == 0) {
             long long off = -1;
             const unsigned long long need = tc_need_bytes(n, G, Gp);
@@ -1103,7 +1103,7 @@ __global__ void k_classify(SolveArgs A, const int* bucket_hi, int nb, int32_t* b
     for (int k = 0; k < nb; ++k)
         if (n <= bucket_hi[k]) { b = k; break; }
     atomicAdd(&bcount[b], 1);
-    if (A.tc_ws != nullptr && n <= A.tc_nmax)
+    if (A.tc_ws != nullptr && n <= max(A.tc_nmax, A.tc_nmax_gl))
         atomicAdd(&A.tc->total, (unsigned long long)tc_need_bytes((int)n, A.G, A.Gp));
 }
 
