@@ -61,6 +61,7 @@ struct PrecPlan {
     int nmax_smem = 0;
     int tc_nmax = 0;      // largest n of the tensor-core variance (0: off)
     int tc_nmax_gl = 0;   // the same for the global-workspace buckets
+    bool fb_tri = true;   // the re-solve launch keeps the factor in shared memory
     int fb_smem = 0, fb_grid = 0;  // regular re-solve of what the variant could not hand over
 };
 
@@ -174,13 +175,14 @@ static int validate(const gp_voxels_config* c)
 
 // Bucket bounds: fixed ladder below max_points, plus the largest n whose factor fits
 // shared memory, capped at kNumBuckets buckets.
-static std::vector<int> bucket_bounds(int maxp, int nmax_smem)
+static std::vector<int> bucket_bounds(int maxp, int nmax_smem, int extra = 0)
 {
     const int ladder[] = {16, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024, 2048};
     std::vector<int> b;
     for (int x : ladder)
         if (x < maxp) b.push_back(x);
     if (nmax_smem < maxp) b.push_back(nmax_smem);
+    if (extra > 0 && extra < maxp) b.push_back(extra);
     b.push_back(maxp);
     std::sort(b.begin(), b.end());
     b.erase(std::unique(b.begin(), b.end()), b.end());
@@ -192,7 +194,18 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
 {
     const gp_voxels_config& c = h->cfg;
     CK(solve_max_smem_n(kind, c.grid_side, h->Gp, &P.nmax_smem));
-    std::vector<int> bounds = bucket_bounds(c.max_points, P.nmax_smem);
+    // tensor-core variance (batch entry, float-float): the variant without the contraction
+    // fits larger voxels in shared memory, so its largest n is a bucket bound of its own
+    P.tc_nmax = 0;
+    P.tc_nmax_gl = 0;
+    const bool tc_on = kind == PREC_FF && h->main.tc_cap > 0;
+    if (tc_on) {
+        int nmax_tcv = 0;
+        CK(solve_max_smem_n(kind, c.grid_side, h->Gp, &nmax_tcv, true));
+        P.tc_nmax = std::min(std::min(kTcMaxN, c.max_points), std::max(nmax_tcv, P.nmax_smem));
+        P.tc_nmax_gl = std::min(kTcMaxNGl, c.max_points);
+    }
+    std::vector<int> bounds = bucket_bounds(c.max_points, P.nmax_smem, P.tc_nmax);
     P.nb = (int)bounds.size();
     int hi_host[kNumBuckets];
     for (int i = 0; i < P.nb; ++i) {
@@ -215,19 +228,13 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         B.grid = B.tri_smem ? h->sms * occ : h->gws_grid;
         B.tcv_ok = false;
     }
-    // tensor-core variance (batch entry, float-float): the variant without the contraction
-    // for every shared-memory bucket up to its largest n
-    P.tc_nmax = 0;
-    P.tc_nmax_gl = 0;
-    if (kind == PREC_FF && h->main.tc_cap > 0) {
-        P.tc_nmax = std::min(std::min(kTcMaxN, c.max_points), P.nmax_smem);
-        P.tc_nmax_gl = std::min(kTcMaxNGl, c.max_points);
+    if (tc_on) {  // the variant for every bucket up to its largest n (shared memory)
         for (int i = 0; i < P.nb; ++i) {
             Bucket& B = P.b[i];
-            if (!B.tri_smem || B.hi > P.tc_nmax) continue;
+            if (B.hi > P.tc_nmax) continue;
             B.tcv_ok = true;
-            B.v.nthr = B.nthr;
-            B.v.percol = B.percol;
+            B.v.nthr = B.tri_smem ? B.nthr : solve_threads(B.hi, true);
+            B.v.percol = B.tri_smem && B.percol;
             B.v.panel = B.panel;
             B.v.smem = smem_plan(B.hi, c.grid_side, h->Gp, 8, true, B.v.nthr, true).total;
             int occ = 0;
@@ -235,11 +242,14 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
             if (occ < 1) return GPV_EINVAL;
             B.v.grid = h->sms * occ;
         }
-        P.fb_smem = smem_plan(P.tc_nmax, c.grid_side, h->Gp, 8, true, 512).total;
+        // the re-solve of what the variant cannot hand over: in shared memory if the regular
+        // plan fits its largest n, else with the factor in the global workspace
+        P.fb_tri = P.tc_nmax <= P.nmax_smem;
+        P.fb_smem = smem_plan(P.fb_tri ? P.tc_nmax : c.max_points, c.grid_side, h->Gp, 8, P.fb_tri, 512).total;
         int occ = 0;
-        CK(solve_occupancy(kind, true, 512, P.fb_smem, &occ));
+        CK(solve_occupancy(kind, P.fb_tri, 512, P.fb_smem, &occ));
         if (occ < 1) return GPV_EINVAL;
-        P.fb_grid = h->sms * occ;
+        P.fb_grid = P.fb_tri ? h->sms * occ : h->gws_grid;
     }
     CK(cudaMalloc(&P.d_hi, sizeof(int) * kNumBuckets));
     CK(cudaMemcpy(P.d_hi, hi_host, sizeof(int) * P.nb, cudaMemcpyHostToDevice));
@@ -289,7 +299,7 @@ static size_t ctx_bytes(const gp_voxels_config* c, int cap, int sms, int Gp)
 static size_t tc_bytes(const gp_voxels_config* c, int Gp, size_t rest)
 {
     if (c->precision != GPV_PREC_MIXED || c->tc_workspace_mb <= 0) return 0;
-    const int nmax = std::min(kTcMaxN, c->max_points);
+    const int nmax = std::min(std::max(kTcMaxN, kTcMaxNGl), c->max_points);
     size_t b = std::min((size_t)c->tc_workspace_mb << 20,
                         (size_t)c->max_voxels * (size_t)tc_need_bytes(nmax, c->grid_side, Gp));
     b += (size_t)c->max_voxels * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
@@ -590,15 +600,16 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     int used = 0;
     for (int b = P.nb - 1; b >= 0; --b) {
         const Bucket& B = P.b[b];
-        const int si = B.tri_smem ? 1 + b : 0;
+        const bool tcv = a.tc_ws && B.tcv_ok;  // the variant, factor in shared memory
+        const int si = (B.tri_smem || tcv) ? 1 + b : 0;
         cudaStream_t ss = x.side[si % kNumBuckets];
         CK(cudaStreamWaitEvent(ss, x.ev_fork, 0));
         a.work = x.d_work;
         a.work_base = x.d_bbase + b;
         a.work_count = x.d_bcount + b;
         a.work_next = x.d_next + b;
-        a.nmax = B.tri_smem ? B.hi : c.max_points;
-        if (a.tc_ws && B.tcv_ok) {  // the variance goes to the tensor cores
+        a.nmax = (B.tri_smem || tcv) ? B.hi : c.max_points;
+        if (tcv) {  // the variance goes to the tensor cores
             a.percol_max = B.v.percol ? B.hi : 0;
             a.panel = B.v.panel;
             CK(launch_solve(kind, true, B.v.nthr, a, B.v.grid, B.v.smem, ss, true));
@@ -634,10 +645,10 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             f.work_base = nullptr;
             f.work_count = &a.tc->fb_count;
             f.work_next = &a.tc->fb_next;
-            f.nmax = P.tc_nmax;
+            f.nmax = P.fb_tri ? P.tc_nmax : c.max_points;
             f.percol_max = default_percol_max(8);
             f.panel = 16;
-            CK(launch_solve(kind, true, 512, f, P.fb_grid, P.fb_smem, s));
+            CK(launch_solve(kind, P.fb_tri, 512, f, P.fb_grid, P.fb_smem, s));
             ++h->last_launches;
         }
         if (a.pos) {
@@ -1083,6 +1094,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
     for (int b = 0; b < P.nb; ++b) {
         Bucket& B = P.b[b];
         const bool tcv = a.tc_ws && B.tcv_ok;  // tune the variant the batch entry launches
+        const bool tri = B.tri_smem || tcv;     // its factor is in shared memory
         float best_ms = 3.0e38f;
         int best = tcv ? B.v.nthr : B.nthr, best_smem = tcv ? B.v.smem : B.smem;
         int best_grid = tcv ? B.v.grid : B.grid;
@@ -1096,21 +1108,21 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
             const int var = ci / 3;  // blocked with 16-, 8- or 4-column panels, or per column
             const bool pc = var == 3;
             const int pw = var == 0 ? 16 : (var == 1 ? 8 : 4);
-            if (var > 0 && !B.tri_smem) continue;  // variants of the shared-memory factor
-            if (B.tri_smem && nt < B.hi) continue;  // the shared-memory variants need n <= CTA size
-            if (!B.tri_smem && nt < 256) continue;
-            const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
-                                          tsize(kind), B.tri_smem, nt, tcv);
-            if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) continue;
+            if (var > 0 && !tri) continue;  // variants of the shared-memory factor
+            if (tri && nt < B.hi) continue;  // the shared-memory variants need n <= CTA size
+            if (!tri && nt < 256) continue;
+            const SmemPlan sp = smem_plan(tri ? B.hi : c.max_points, c.grid_side, h->Gp,
+                                          tsize(kind), tri, nt, tcv);
+            if (!tri && (sp.pb < 4 || sp.rb < 4)) continue;
             int occ = 0;
-            CK(solve_occupancy(kind, B.tri_smem, nt, sp.total, &occ, tcv));
+            CK(solve_occupancy(kind, tri, nt, sp.total, &occ, tcv));
             if (occ < 1) continue;
-            const int grid = B.tri_smem ? h->sms * occ : h->gws_grid;
+            const int grid = tri ? h->sms * occ : h->gws_grid;
             a.work = x.d_work;
             a.work_base = x.d_bbase + b;
             a.work_count = x.d_bcount + b;
             a.work_next = x.d_next + b;
-            a.nmax = B.tri_smem ? B.hi : c.max_points;
+            a.nmax = tri ? B.hi : c.max_points;
             a.percol_max = pc ? B.hi : 0;
             a.panel = pw;
             float ms = 3.0e38f;
@@ -1120,7 +1132,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
                     CK(cudaMemsetAsync(reinterpret_cast<unsigned char*>(a.tc) + 8, 0,
                                        sizeof(TcCounters) - 8, s));
                 CK(cudaEventRecord(e0, s));
-                CK(launch_solve(kind, B.tri_smem, nt, a, grid, sp.total, s, tcv));
+                CK(launch_solve(kind, tri, nt, a, grid, sp.total, s, tcv));
                 CK(cudaEventRecord(e1, s));
                 CK(cudaEventSynchronize(e1));
                 float t = 0.f;

@@ -105,10 +105,10 @@ constexpr float kTcCond = 1e5f;
 // distributed, their sums stay near 2^18 units) to round.
 constexpr int kTcMaxNGl = 255;
 
-// Largest n of the tensor-core variance: with 8-bit slices of at most 2^7 grid units the FP32
-// sums of the four exact accumulator levels stay below 2^24 units for n < 256 (level 3:
-// 4 x 2^14 n); 192 is the largest shared-memory size bucket.
-constexpr int kTcMaxN = 192;
+// Largest n of the tensor-core variance with the factor in shared memory (the variant's
+// smaller plan fits about 224 points at G = 16); the exactness of the levels is as for
+// the workspace voxels below.
+constexpr int kTcMaxN = 224;
 
 // Workspace bytes of one voxel: packed L^-1, the factors (n G and n Gp), the G^2 means
 // and the G^2 variances, float-float, then the slice exponents of the n rows of L^-1 and
@@ -210,7 +210,7 @@ cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, in
 // tcv: the float-float shared-memory variant that hands the variance to k_var_tc
 cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& a, int grid, int smem,
                          cudaStream_t s, bool tcv = false);
-cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out);
+cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out, bool tcv = false);
 cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm,
                             bool tcv = false);
 cudaError_t launch_var_tc(const SolveArgs& a, int sms, cudaStream_t s);

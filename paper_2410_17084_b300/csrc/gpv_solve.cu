@@ -1180,7 +1180,7 @@ cudaError_t launch_solve(int prec, bool tri_in_smem, int nthr, const SolveArgs& 
 
 static int tsize_of(int prec) { return prec == PREC_F32 ? 4 : 8; }
 
-cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out)
+cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out, bool tcv)
 {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1190,7 +1190,7 @@ cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out)
     const int static_bytes = 6 * 32 * 8 + 32 * 8 + 64 + 256 * 8;
     int best = 0;
     for (int n = 8; n <= 1024; n += 8) {
-        SmemPlan p = smem_plan(n, G, Gp, tsize_of(prec), true, solve_threads(n, true));
+        SmemPlan p = smem_plan(n, G, Gp, tsize_of(prec), true, solve_threads(n, true), tcv);
         if (p.total + static_bytes <= optin) best = n;
     }
     *nmax_out = best;

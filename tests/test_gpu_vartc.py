@@ -113,14 +113,18 @@ def test_tc_grid_sides(gpv, oracle, shape):
 
 
 def test_tc_largest_eligible_voxels(gpv, oracle):
-    """n = 180..192 (the largest n of the tensor-core variance), next to n just above it
-    (193..200: CUDA-core variance in the same call, factor in the global workspace)."""
+    """n = 180..200 across the 192-point bound of the regular shared-memory plan: above it
+    the tensor-core variant still factors in shared memory (bucket up to 224 points)."""
     b = _quadric(120, seed=35, lo=180, hi=200, pool=20000)
     assert (b.counts > 192).any() and (b.counts <= 192).any()
     tc, _ = _run(gpv, b, max_points=256)
     cc, _ = _run(gpv, b, max_points=256, tc_workspace_mb=0)
     solved = _oracle_check(b, tc, oracle, "tc n 180..200")
-    _agree(b, tc, cc, solved, "tc n 180..200")
+    # with the tensor-core variance on, 193..224-point voxels factor in shared memory (the
+    # variant's smaller plan fits them); off, in the global workspace: the means agree to
+    # rounding, not bit for bit
+    assert np.abs(tc["mean"] - cc["mean"])[solved].max() <= 1e-7
+    _agree(b, tc, cc, solved, "tc n 180..200", exact_mean=False)
 
 
 def test_tc_workspace_too_small_falls_back_whole_call(gpv):
