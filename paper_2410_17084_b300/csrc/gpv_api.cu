@@ -233,9 +233,12 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
             Bucket& B = P.b[i];
             if (B.hi > P.tc_nmax) continue;
             B.tcv_ok = true;
-            B.v.nthr = B.tri_smem ? B.nthr : solve_threads(B.hi, true);
-            B.v.percol = B.tri_smem && B.percol;
-            B.v.panel = B.panel;
+            // defaults as the autotuner picks them on the quadric workload: without the
+            // contraction, 256-thread CTAs (three per SM) beat 512 for blocked factors,
+            // 128-thread per-column ones for the small buckets
+            B.v.nthr = B.hi <= 64 ? 128 : 256;
+            B.v.percol = c.factor_panel == 0 && B.hi <= 64;
+            B.v.panel = c.factor_panel > 0 ? c.factor_panel : 4;
             B.v.smem = smem_plan(B.hi, c.grid_side, h->Gp, 8, true, B.v.nthr, true).total;
             int occ = 0;
             CK(solve_occupancy(kind, true, B.v.nthr, B.v.smem, &occ, true));

@@ -6,8 +6,8 @@ on the CUDA cores (tc_workspace_mb = 0).
 Tolerances: the oracle tolerances of the mixed path (mean 1e-4 m, variance 1e-3 relative
 to max(var_ref, 1e-3 sigma^2), scale 1e-4, rotation 1e-3 rad).  Both variance paths carry
 about 48 bits before the cancellation in sf2 - |v|^2, so they agree far more tightly:
-|var_tc - var_cc| <= 1e-6 max(var_cc, 1e-3 sigma^2) and the means are identical (the mean
-does not go through the tensor cores).
+|var_tc - var_cc| <= 1e-6 max(var_cc, 1e-3 sigma^2), and the means (which do not go through
+the tensor cores) to 1e-7 m: the two runs may factor with different CTA sizes and panels.
 """
 import numpy as np
 import pytest
@@ -66,9 +66,12 @@ def _oracle_check(b, out, oracle, name, init=True):
     return solved
 
 
-def _agree(b, tc, cc, solved, name, exact_mean=True):
+def _agree(b, tc, cc, solved, name, exact_mean=False):
+    # the two runs may factor with different launch configurations (the variant without the
+    # contraction has defaults and a shared-memory plan of its own): means agree to rounding
     if exact_mean:
         assert np.array_equal(tc["mean"], cc["mean"]), name
+    assert np.abs(tc["mean"] - cc["mean"])[solved].max() <= 1e-7, name
     floor = 1e-3 * b.sn2.astype(np.float64)[:, None]
     rel = np.abs(tc["var"].astype(np.float64) - cc["var"]) / np.maximum(cc["var"], floor)
     worst = float(rel[solved].max()) if solved.any() else 0.0
@@ -123,8 +126,7 @@ def test_tc_largest_eligible_voxels(gpv, oracle):
     # with the tensor-core variance on, 193..224-point voxels factor in shared memory (the
     # variant's smaller plan fits them); off, in the global workspace: the means agree to
     # rounding, not bit for bit
-    assert np.abs(tc["mean"] - cc["mean"])[solved].max() <= 1e-7
-    _agree(b, tc, cc, solved, "tc n 180..200", exact_mean=False)
+    _agree(b, tc, cc, solved, "tc n 180..200")
 
 
 def test_tc_workspace_too_small_falls_back_whole_call(gpv):
@@ -139,8 +141,7 @@ def test_tc_workspace_too_small_falls_back_whole_call(gpv):
         assert np.array_equal(small[k], again[k]), k
     assert np.array_equal(small["status"], off["status"])
     solved = (off["status"].astype(np.uint32) & 0x45) == 0
-    assert np.abs(small["mean"] - off["mean"])[solved].max() <= 1e-7
-    _agree(b, small, off, solved, "workspace full", exact_mean=False)
+    _agree(b, small, off, solved, "workspace full")
 
 
 def test_tc_repeatable(gpv):
