@@ -115,14 +115,16 @@ typedef struct {
                             points, else blocked with 16-column panels); 4, 8 or 16: the
                             blocked shared-memory Cholesky with that panel width for every
                             voxel; gp_voxels_autotune may choose otherwise per size bucket */
-    int tc_workspace_mb; /* GPV_PREC_MIXED batch solves: MiB of device workspace for the
+    int tc_workspace_mb; /* GPV_PREC_MIXED solves: MiB of device workspace, in total, for the
                             posterior variance on the tensor cores (Eq. 3, diag(Sigma*) by
-                            exact BF16 slice products; voxels of up to 192 points whose factor
-                            fits shared memory).  A call whose eligible voxels need more than
-                            this forms every variance on the CUDA cores instead, so the
-                            choice never depends on scheduling.  0 turns it off; default
-                            4096; capped by what max_voxels voxels could use and, under
-                            mem_budget, by what the budget leaves. */
+                            exact BF16 slice products; well-conditioned voxels of up to 255
+                            points).  Split evenly between the batch entry and, with the
+                            voxel store on, each scan slot; each share is capped by what
+                            its voxels (max_voxels, max_scan_voxels) could use and, under
+                            mem_budget, by what the budget leaves; a share below 16 MiB is
+                            dropped.  A call whose eligible voxels need more than its share
+                            forms every variance on the CUDA cores instead, so the choice
+                            never depends on scheduling.  0 turns it off; default 4096. */
 } gp_voxels_config;
 
 /* Voxel types of Sec. 3.3 (gp_voxels_scan_types, gp_voxels_type_counts). */

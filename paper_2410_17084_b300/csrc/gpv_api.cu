@@ -194,11 +194,12 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
 {
     const gp_voxels_config& c = h->cfg;
     CK(solve_max_smem_n(kind, c.grid_side, h->Gp, &P.nmax_smem));
-    // tensor-core variance (batch entry, float-float): the variant without the contraction
-    // fits larger voxels in shared memory, so its largest n is a bucket bound of its own
+    // tensor-core variance (float-float; the batch entry or the scan slots have a
+    // workspace): the variant without the contraction fits larger voxels in shared memory,
+    // so its largest n is a bucket bound of its own
     P.tc_nmax = 0;
     P.tc_nmax_gl = 0;
-    const bool tc_on = kind == PREC_FF && h->main.tc_cap > 0;
+    const bool tc_on = kind == PREC_FF && (h->main.tc_cap > 0 || (h->sctx && h->sctx[0].tc_cap > 0));
     if (tc_on) {
         int nmax_tcv = 0;
         CK(solve_max_smem_n(kind, c.grid_side, h->Gp, &nmax_tcv, true));
@@ -296,19 +297,41 @@ static size_t ctx_bytes(const gp_voxels_config* c, int cap, int sms, int Gp)
     return b;
 }
 
-// Workspace of the tensor-core variance of the batch entry: the configured size, no more
-// than max_voxels voxels of the largest eligible n could use, and (under a memory
-// budget) what the budget leaves; below 16 MB it is not worth keeping.
-static size_t tc_bytes(const gp_voxels_config* c, int Gp, size_t rest)
+// Queue lists of the tensor-core variance for a context of cap voxels.
+static size_t tc_lists(int cap)
 {
-    if (c->precision != GPV_PREC_MIXED || c->tc_workspace_mb <= 0) return 0;
+    return (size_t)cap * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
+           sizeof(int32_t) * kNumBuckets;
+}
+
+// Workspaces of the tensor-core variance, per solve context: the batch entry's and, when
+// the store is on, each serving scan slot's (slots may be in flight together, so each needs
+// its own).  The configured size is split evenly between the contexts; each share is capped
+// by what the context's voxels of the largest eligible n could use and, under a memory
+// budget, by what the budget leaves.  A share below 16 MB is not worth keeping.  Returned
+// sizes include the queue lists; 0 means off for that context.
+struct TcSplit { size_t main = 0, slot = 0; };
+
+static TcSplit tc_split(const gp_voxels_config* c, int Gp, size_t rest)
+{
+    TcSplit t;
+    if (c->precision != GPV_PREC_MIXED || c->tc_workspace_mb <= 0) return t;
     const int nmax = std::min(std::max(kTcMaxN, kTcMaxNGl), c->max_points);
-    size_t b = std::min((size_t)c->tc_workspace_mb << 20,
-                        (size_t)c->max_voxels * (size_t)tc_need_bytes(nmax, c->grid_side, Gp));
-    b += (size_t)c->max_voxels * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
-         sizeof(int32_t) * kNumBuckets;
-    if (c->mem_budget) b = c->mem_budget > rest ? std::min(b, c->mem_budget - rest) : 0;
-    return b < ((size_t)16 << 20) ? 0 : b;
+    const size_t per = tc_need_bytes(nmax, c->grid_side, Gp);
+    const int slots = c->hash_capacity > 0 ? c->scan_slots : 0;
+    size_t share = ((size_t)c->tc_workspace_mb << 20) / (size_t)(1 + slots);
+    if (c->mem_budget) {
+        const size_t lists = tc_lists(c->max_voxels) + (size_t)slots * tc_lists(c->max_scan_voxels);
+        const size_t left = c->mem_budget > rest + lists ? c->mem_budget - rest - lists : 0;
+        share = std::min(share, left / (size_t)(1 + slots));
+    }
+    auto one = [&](int cap) -> size_t {
+        const size_t ws = std::min(share, (size_t)cap * per);
+        return ws < ((size_t)16 << 20) ? 0 : ws + tc_lists(cap);
+    };
+    t.main = one(c->max_voxels);
+    if (slots > 0) t.slot = one(c->max_scan_voxels);
+    return t;
 }
 
 static size_t solve_bytes(const gp_voxels_config* c, int sms, int Gp)
@@ -323,7 +346,8 @@ static size_t solve_bytes(const gp_voxels_config* c, int sms, int Gp)
 static size_t solve_bytes_tc(const gp_voxels_config* c, int sms, int Gp)
 {
     const size_t rest = solve_bytes(c, sms, Gp) + store_bytes(c);
-    return rest + tc_bytes(c, Gp, rest);
+    const TcSplit t = tc_split(c, Gp, rest);
+    return rest + t.main + (c->hash_capacity > 0 ? (size_t)c->scan_slots * t.slot : 0);
 }
 
 extern "C" int gp_voxels_query_sizes(const gp_voxels_config* c, size_t* bytes_out)
@@ -392,9 +416,7 @@ static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap, size_t tc_total = 0)
     AL(x.d_esc_count, sizeof(int32_t) * 2);
     AL(x.d_gws, 8 * (size_t)h->gws_stride * (size_t)h->gws_grid);
     if (tc_total > 0) {
-        const size_t lists = (size_t)cap * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
-                             sizeof(int32_t) * kNumBuckets;
-        x.tc_cap = tc_total - lists;
+        x.tc_cap = tc_total - tc_lists(cap);
         AL(x.d_tc_ws, x.tc_cap);
         AL(x.d_tc, sizeof(TcCounters));
         AL(x.d_tc_v, sizeof(int32_t) * (size_t)cap);
@@ -428,7 +450,7 @@ static int create_impl(gp_voxels_t* h)
     h->gws_grid = 2 * h->sms;
     const size_t need_rest = solve_bytes(&c, h->sms, h->Gp) + store_bytes(&c);
     if (c.mem_budget && need_rest > c.mem_budget) return GPV_EBUDGET;
-    const size_t need_tc = tc_bytes(&c, h->Gp, need_rest);
+    const TcSplit need_tc = tc_split(&c, h->Gp, need_rest);
     const size_t mv = (size_t)c.max_voxels;
     auto alloc = [&](void** p, size_t bytes) -> int {
         cudaError_t e = cudaMalloc(p, bytes);
@@ -444,13 +466,13 @@ static int create_impl(gp_voxels_t* h)
     AL(h->d_pl_next, sizeof(int32_t) * mv);
 #undef AL
     h->gws_stride = gws_slice_elems(c.max_points, c.grid_side, h->Gp);
-    if ((rc = ctx_create(h, h->main, c.max_voxels, need_tc)) != GPV_OK) return rc;
-    if (need_tc > 0) CK(var_tc_prepare());
+    if ((rc = ctx_create(h, h->main, c.max_voxels, need_tc.main)) != GPV_OK) return rc;
+    if (need_tc.main > 0 || (c.hash_capacity > 0 && need_tc.slot > 0)) CK(var_tc_prepare());
     if (c.hash_capacity > 0) {
         h->sctx = new (std::nothrow) SolveCtx[c.scan_slots];
         if (!h->sctx) return GPV_ENOMEM;
         for (int i = 0; i < c.scan_slots; ++i)
-            if ((rc = ctx_create(h, h->sctx[i], c.max_scan_voxels)) != GPV_OK) return rc;
+            if ((rc = ctx_create(h, h->sctx[i], c.max_scan_voxels, need_tc.slot)) != GPV_OK) return rc;
     }
     const int one = 1;
     CK(cudaMemcpy(h->d_one, &one, sizeof(int), cudaMemcpyHostToDevice));

@@ -71,3 +71,20 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(g, "_lib", None)
     with pytest.raises(RuntimeError):
         g.lib()
+
+
+def test_tensor_core_workspace_split_between_contexts(libpath):
+    """The tensor-core variance workspace (tc_workspace_mb) is one total, split evenly between
+    the batch entry and the serving scan slots, and a memory budget bounds the whole handle."""
+    from paper_2410_17084_b300 import gp_voxels as g
+    from paper_2410_17084_b300 import serve
+    mb = 1 << 20
+    for slots in (1, 4):
+        off = g.gp_voxels_query_sizes(serve.serving_config(mem_budget=0, scan_slots=slots,
+                                                           tc_workspace_mb=0))
+        on = g.gp_voxels_query_sizes(serve.serving_config(mem_budget=0, scan_slots=slots))
+        lists = ((1 << 16) + slots * (1 << 15)) * 24 + (slots + 1) * 4096
+        assert 4095 * mb < on - off <= 4096 * mb + lists
+    budgeted = serve.serving_config()
+    assert g.gp_voxels_query_sizes(budgeted) <= budgeted.mem_budget
+    assert g.gp_voxels_query_sizes(budgeted) > budgeted.mem_budget - 16 * mb

@@ -83,6 +83,33 @@ def test_same_result_alone_and_in_the_mix(env):
             assert np.array_equal(outs[0][k][key], outs[1][k][key]), (k, key)
 
 
+def test_scan_slots_take_the_tensor_core_variance(env):
+    """Each scan slot has its share of the tensor-core workspace: concurrent scans form the
+    variance on the tensor cores (more kernels per solve) and agree with the same scans solved
+    with the workspace off to 1e-6 relative (floor 1e-3 sigma^2), means to 1e-7 m."""
+    gv, serve, synth, scene, scans = env
+    outs, launches = [], []
+    for mb in (4096, 0):
+        srv = serve.Server(_cfg(serve, tc_workspace_mb=mb))
+        lat, wall, res = srv.run(scans, collect=True, realtime=False, max_inflight=4)
+        launches.append(gv.gp_voxels_last_launches(srv.g.h))
+        srv.close()
+        outs.append(res)
+    assert launches[0] > launches[1] + 2, launches
+    floor = 1e-3 * _cfg(serve).sn2
+    worst = 0.0
+    for k in range(len(scans)):
+        a, b = outs[0][k], outs[1][k]
+        assert np.array_equal(a["status"], b["status"]) and np.array_equal(a["keys"], b["keys"])
+        st = b["status"].astype(np.uint32)
+        solved = (st & (gv.VOX_BELOW_TAU | gv.VOX_NOT_SPD)) == 0
+        assert np.abs(a["mean"] - b["mean"])[solved].max() <= 1e-7
+        rel = np.abs(a["var"].astype(np.float64) - b["var"]) / np.maximum(b["var"], floor)
+        worst = max(worst, float(rel[solved].max()))
+    print(f"\nscan slots: tensor-core vs CUDA-core variance, max rel {worst:.2e}")
+    assert worst <= 1e-6
+
+
 def test_admission_by_free_slots(env):
     import torch
     gv, serve, synth, scene, scans = env
