@@ -129,6 +129,20 @@ def test_tc_largest_eligible_voxels(gpv, oracle):
     _agree(b, tc, cc, solved, "tc n 180..200")
 
 
+def test_tc_global_workspace_voxels(gpv, oracle):
+    """n = 216..256 across the 224-point bound of the variant's shared-memory plan: above it
+    the factor lives in the global workspace and the variance still goes to the tensor cores
+    up to 255 points; 256-point voxels form it on the CUDA cores."""
+    b = _quadric(120, seed=39, lo=216, hi=256, pool=40000)
+    assert (b.counts <= 224).any() and ((b.counts > 224) & (b.counts < 256)).any()
+    assert (b.counts == 256).any()
+    tc, l_tc = _run(gpv, b, max_points=256)
+    cc, l_cc = _run(gpv, b, max_points=256, tc_workspace_mb=0)
+    assert l_tc > l_cc + 2
+    solved = _oracle_check(b, tc, oracle, "tc n 216..256")
+    _agree(b, tc, cc, solved, "tc n 216..256")
+
+
 def test_tc_workspace_too_small_falls_back_whole_call(gpv):
     """A call whose eligible voxels need more workspace than configured forms every
     variance on the CUDA cores (the regular kernel re-solves them): it agrees with the
