@@ -264,6 +264,21 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                 const int j = j0 + r;
                 const int Ej = j < n ? EX[j] : 0;
                 uint32_t started = 0u;  // accumulators written in this pass (thread 0)
+                // operands of a chunk, loaded one chunk ahead: their latency overlaps the
+                // barrier and the MMA issue of the chunk before
+                ff pa[kKE], pb[kKE], px[kKE];
+                auto load_chunk = [&](int kc) {
+                    const int i0 = kc * kKC + kKE * h;
+#pragma unroll
+                    for (int e = 0; e < kKE; ++e) {
+                        const int i = i0 + e;
+                        const bool ia = qv && i < n;
+                        pa[e] = ia ? FA[i * G + u] : zero<ff>();
+                        pb[e] = ia ? FB[i * Gp + w] : zero<ff>();
+                        px[e] = (j < n && i <= j) ? X[tri_off_p(i, n) + j - i] : zero<ff>();
+                    }
+                };
+                load_chunk(0);
                 for (int kc = 0; kc < nkc; ++kc) {
                     const int b = chunk & 1;
                     if (uses[b] > 0) {  // the MMAs that last read this buffer are done
@@ -272,14 +287,11 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                     }
                     unsigned char* abuf = sm + kOffA + b * kSl * kSliceBytes;
                     unsigned char* bbuf = sm + kOffB + b * kSl * kSliceBytes;
-                    const int i0 = kc * kKC + kKE * h;
                     {   // A: k(x_i, q) = a_i(u) b_i(v) for the 128 queries of the tile
                         float hi[kKE], lo[kKE];
 #pragma unroll
                         for (int e = 0; e < kKE; ++e) {
-                            const int i = i0 + e;
-                            ff k = zero<ff>();
-                            if (qv && i < n) k = FA[i * G + u] * FB[i * Gp + w];
+                            const ff k = pa[e] * pb[e];  // zero past n and past G^2
                             hi[e] = k.hi;
                             lo[e] = k.lo;
                         }
@@ -289,14 +301,12 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                         float hi[kKE], lo[kKE];
 #pragma unroll
                         for (int e = 0; e < kKE; ++e) {
-                            const int i = i0 + e;
-                            ff x = zero<ff>();
-                            if (j < n && i <= j) x = X[tri_off_p(i, n) + j - i];
-                            hi[e] = x.hi;
-                            lo[e] = x.lo;
+                            hi[e] = px[e].hi;
+                            lo[e] = px[e].lo;
                         }
                         store_row<kKE>(bbuf, r, kKE * h, hi, lo, Ej);
                     }
+                    if (kc + 1 < nkc) load_chunk(kc + 1);
                     umma::fence_proxy_async_smem();
                     __syncthreads();
                     if (tid == 0) {
