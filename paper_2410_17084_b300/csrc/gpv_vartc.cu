@@ -281,34 +281,37 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                 load_chunk(0);
                 for (int kc = 0; kc < nkc; ++kc) {
                     const int b = chunk & 1;
-                    if (uses[b] > 0) {  // the MMAs that last read this buffer are done
-                        const bool ok = umma::mbar_wait(&mbar[b], (uses[b] - 1) & 1, kPolls);
-                        if (__syncthreads_or(!ok)) { failed = true; break; }
-                    }
+                    // each thread sees for itself that the MMAs which last read this buffer
+                    // are done before it writes there; a wait that gave up skips the writes
+                    // and is shared at the barrier below
+                    bool bad = false;
+                    if (uses[b] > 0) bad = !umma::mbar_wait(&mbar[b], (uses[b] - 1) & 1, kPolls);
                     unsigned char* abuf = sm + kOffA + b * kSl * kSliceBytes;
                     unsigned char* bbuf = sm + kOffB + b * kSl * kSliceBytes;
-                    {   // A: k(x_i, q) = a_i(u) b_i(v) for the 128 queries of the tile
-                        float hi[kKE], lo[kKE];
+                    if (!bad) {
+                        {   // A: k(x_i, q) = a_i(u) b_i(v) for the 128 queries of the tile
+                            float hi[kKE], lo[kKE];
 #pragma unroll
-                        for (int e = 0; e < kKE; ++e) {
-                            const ff k = pa[e] * pb[e];  // zero past n and past G^2
-                            hi[e] = k.hi;
-                            lo[e] = k.lo;
+                            for (int e = 0; e < kKE; ++e) {
+                                const ff k = pa[e] * pb[e];  // zero past n and past G^2
+                                hi[e] = k.hi;
+                                lo[e] = k.lo;
+                            }
+                            store_row<kKE>(abuf, r, kKE * h, hi, lo, F);
                         }
-                        store_row<kKE>(abuf, r, kKE * h, hi, lo, F);
-                    }
-                    {   // B: row j of L^-1, zero above the diagonal and past n
-                        float hi[kKE], lo[kKE];
+                        {   // B: row j of L^-1, zero above the diagonal and past n
+                            float hi[kKE], lo[kKE];
 #pragma unroll
-                        for (int e = 0; e < kKE; ++e) {
-                            hi[e] = px[e].hi;
-                            lo[e] = px[e].lo;
+                            for (int e = 0; e < kKE; ++e) {
+                                hi[e] = px[e].hi;
+                                lo[e] = px[e].lo;
+                            }
+                            store_row<kKE>(bbuf, r, kKE * h, hi, lo, Ej);
                         }
-                        store_row<kKE>(bbuf, r, kKE * h, hi, lo, Ej);
                     }
                     if (kc + 1 < nkc) load_chunk(kc + 1);
                     umma::fence_proxy_async_smem();
-                    __syncthreads();
+                    if (__syncthreads_or(bad)) { failed = true; break; }
                     if (tid == 0) {
                         umma::fence_after_sync();
                         const uint32_t idesc = umma::idesc_bf16(kMT, Np);
