@@ -26,16 +26,19 @@
 // of 80 columns.
 //
 // Organisation.  Each size bucket launches this kernel on its own stream right after its
-// solve launch, over the same work list, so the variance of small voxels overlaps the
-// factors of large ones.  One persistent CTA per SM (512 threads) owns the tensor memory:
-// five or six accumulators of 128 lanes (the queries of one M tile) x up to 96 or 80
-// columns (rows j of L^-1 per pass).  For each 16-wide chunk of i, all threads cut the A slices (K*^T: 128
-// queries x 16) and the B slices (L^-1: up to 96 rows x 16) into one of two shared-memory
-// buffers while the tensor core works on the other; one thread issues the 21 MMAs
-// (kind::f16, M = 128, N = rows of the pass, K = 16) and commits them to the buffer's
-// mbarrier.  The epilogue reads the accumulators with tcgen05.ld: lane = query, so each
-// thread sums its own query's norm with no cross-thread reduction.  Every wait is
-// bounded; a wait that gives up marks the voxel GPV_VOX_FAILED.
+// solve launch, over the same work list, so it runs while other buckets still factor; a CTA
+// of it holds most of an SM's registers and all of its tensor memory, so on each SM the two
+// kernels take turns, and this kernel's own speed adds to the step.  One persistent CTA
+// per SM (512 threads) owns the tensor memory: five or six accumulators of 128 lanes (the
+// queries of one M tile) x up to 96 or 80 columns (rows j of L^-1 per pass).  For each
+// 16-wide chunk of i, all threads cut the A slices (K*^T: 128 queries x 16) and the B
+// slices (L^-1: up to 96 rows x 16) into one of two shared-memory buffers while the tensor
+// core works on the other, with the next chunk's operands already on their way from
+// memory; after one barrier, one thread issues the 21 MMAs (kind::f16, M = 128, N = rows
+// of the pass, K = 16) and commits them to the buffer's mbarrier, which each thread checks
+// before it writes that buffer again.  The epilogue reads the accumulators with
+// tcgen05.ld: lane = query, so each thread sums its own query's norm with no cross-thread
+// reduction.  Every wait is bounded; a wait that gives up marks the voxel GPV_VOX_FAILED.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
