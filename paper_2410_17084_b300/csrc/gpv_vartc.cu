@@ -65,8 +65,12 @@ constexpr uint32_t kPolls = 1u << 26;
 
 // dynamic shared memory (bytes)
 constexpr int kOffA = 0;                                   // [2][kSl] A chunks
-constexpr int kOffB = kOffA + 2 * kSl * kSliceBytes;       // [2][kSl] B chunks
-constexpr int kOffNrm = kOffB + 2 * kSl * kSliceBytes;     // ff partial norms [kParts][kMT]
+// B chunk slots: a voxel of one pass (n <= 96) with more than one M tile keeps the slices
+// of every chunk of L^-1 (at most six) for all its tiles; other voxels use two as stages
+constexpr int kBSlots = 6;
+static_assert(kNJ5 <= kBSlots * kKC, "a one-pass voxel has at most kBSlots chunks");
+constexpr int kOffB = kOffA + 2 * kSl * kSliceBytes;       // [kBSlots][kSl] B chunks
+constexpr int kOffNrm = kOffB + kBSlots * kSl * kSliceBytes;  // ff partial norms [kParts][kMT]
 constexpr int kOffEnd = kOffNrm + kParts * kMT * 8;
 // at least 120 KB, more than half an SM's shared memory, so that one CTA per SM holds
 // the tensor memory
@@ -255,7 +259,10 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
         // near 2^-48 of the row scale) and a pass takes 96 rows; above, level 4 is exact too
         const int nlv = n > kLv5MaxN ? kLv : kLv - 1;
         const int njp = n > kLv5MaxN ? kNJ : kNJ5;
+        // one pass and several M tiles: L^-1 is cut once, during the first tile
+        const bool keepB = n <= njp && GG > kMT;
         for (int mt = 0; mt * kMT < GG && !failed; ++mt) {
+            const bool cutB = !keepB || mt == 0;
             const int q = mt * kMT + r;
             const bool qv = q < GG;
             const int u = qv ? q / G : 0, w = qv ? q - u * G : 0;
@@ -278,7 +285,7 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                         const bool ia = qv && i < n;
                         pa[e] = ia ? FA[i * G + u] : zero<ff>();
                         pb[e] = ia ? FB[i * Gp + w] : zero<ff>();
-                        px[e] = (j < n && i <= j) ? X[tri_off_p(i, n) + j - i] : zero<ff>();
+                        px[e] = (cutB && j < n && i <= j) ? X[tri_off_p(i, n) + j - i] : zero<ff>();
                     }
                 };
                 load_chunk(0);
@@ -290,7 +297,8 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                     bool bad = false;
                     if (uses[b] > 0) bad = !umma::mbar_wait(&mbar[b], (uses[b] - 1) & 1, kPolls);
                     unsigned char* abuf = sm + kOffA + b * kSl * kSliceBytes;
-                    unsigned char* bbuf = sm + kOffB + b * kSl * kSliceBytes;
+                    const int bs = keepB ? kc : b;  // B slot: its earlier readers finished
+                    unsigned char* bbuf = sm + kOffB + bs * kSl * kSliceBytes;  // by the last pass end
                     if (!bad) {
                         {   // A: k(x_i, q) = a_i(u) b_i(v) for the 128 queries of the tile
                             float hi[kKE], lo[kKE];
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                             }
                             store_row<kKE>(abuf, r, kKE * h, hi, lo, F);
                         }
-                        {   // B: row j of L^-1, zero above the diagonal and past n
+                        if (cutB) {   // B: row j of L^-1, zero above the diagonal and past n
                             float hi[kKE], lo[kKE];
 #pragma unroll
                             for (int e = 0; e < kKE; ++e) {
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(kVT, 1) k_var_tc(SolveArgs A)
                         umma::fence_after_sync();
                         const uint32_t idesc = umma::idesc_bf16(kMT, Np);
                         const uint32_t a0 = abase + b * kSl * kSliceBytes;
-                        const uint32_t b0 = bbase + b * kSl * kSliceBytes;
+                        const uint32_t b0 = bbase + bs * kSl * kSliceBytes;
 #pragma unroll
                         for (int s = 0; s < kSl; ++s)
 #pragma unroll
