@@ -34,7 +34,8 @@
 // 16-wide chunk of i, all threads cut the A slices (K*^T: 128 queries x 16) and the B
 // slices (L^-1: up to 96 rows x 16) into one of two shared-memory buffers while the tensor
 // core works on the other, with the next chunk's operands already on their way from
-// memory; after one barrier, one thread issues the 21 MMAs (kind::f16, M = 128, N = rows
+// memory (a voxel of one pass keeps the L^-1 slices of all its chunks for its second M
+// tile); after one barrier, one thread issues the 21 MMAs (kind::f16, M = 128, N = rows
 // of the pass, K = 16) and commits them to the buffer's mbarrier, which each thread checks
 // before it writes that buffer again.  The epilogue reads the accumulators with
 // tcgen05.ld: lane = query, so each thread sums its own query's norm with no cross-thread
