@@ -119,7 +119,8 @@ typedef struct {
                             posterior variance on the tensor cores (Eq. 3, diag(Sigma*) by
                             exact BF16 slice products; well-conditioned voxels of up to 255
                             points).  Split evenly between the batch entry and, with the
-                            voxel store on, each scan slot; each share is capped by what
+                            voxel store on and the state machine off (eta <= 0), each
+                            scan slot; each share is capped by what
                             its voxels (max_voxels, max_scan_voxels) could use and, under
                             mem_budget, by what the budget leaves; a share below 16 MiB is
                             dropped.  A call whose eligible voxels need more than its share

@@ -305,11 +305,13 @@ static size_t tc_lists(int cap)
 }
 
 // Workspaces of the tensor-core variance, per solve context: the batch entry's and, when
-// the store is on, each serving scan slot's (slots may be in flight together, so each needs
-// its own).  The configured size is split evenly between the contexts; each share is capped
-// by what the context's voxels of the largest eligible n could use and, under a memory
-// budget, by what the budget leaves.  A share below 16 MB is not worth keeping.  Returned
-// sizes include the queue lists; 0 means off for that context.
+// the store is on without the voxel state machine, each serving scan slot's (slots may be
+// in flight together, so each needs its own; with the state machine the scans solve few,
+// mostly small voxels, whose variance the CUDA cores form sooner than the extra launches
+// of the tensor-core path).  The configured size is split evenly between the contexts;
+// each share is capped by what the context's voxels of the largest eligible n could use
+// and, under a memory budget, by what the budget leaves.  A share below 16 MB is not worth
+// keeping.  Returned sizes include the queue lists; 0 means off for that context.
 struct TcSplit { size_t main = 0, slot = 0; };
 
 static TcSplit tc_split(const gp_voxels_config* c, int Gp, size_t rest)
@@ -318,7 +320,7 @@ static TcSplit tc_split(const gp_voxels_config* c, int Gp, size_t rest)
     if (c->precision != GPV_PREC_MIXED || c->tc_workspace_mb <= 0) return t;
     const int nmax = std::min(std::max(kTcMaxN, kTcMaxNGl), c->max_points);
     const size_t per = tc_need_bytes(nmax, c->grid_side, Gp);
-    const int slots = c->hash_capacity > 0 ? c->scan_slots : 0;
+    const int slots = (c->hash_capacity > 0 && !(c->eta > 0.f)) ? c->scan_slots : 0;
     size_t share = ((size_t)c->tc_workspace_mb << 20) / (size_t)(1 + slots);
     if (c->mem_budget) {
         const size_t lists = tc_lists(c->max_voxels) + (size_t)slots * tc_lists(c->max_scan_voxels);

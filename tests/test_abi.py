@@ -75,7 +75,8 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
 
 def test_tensor_core_workspace_split_between_contexts(libpath):
     """The tensor-core variance workspace (tc_workspace_mb) is one total, split evenly between
-    the batch entry and the serving scan slots, and a memory budget bounds the whole handle."""
+    the batch entry and the serving scan slots (without the voxel state machine), and a
+    memory budget bounds the whole handle."""
     from paper_2410_17084_b300 import gp_voxels as g
     from paper_2410_17084_b300 import serve
     mb = 1 << 20
@@ -88,3 +89,9 @@ def test_tensor_core_workspace_split_between_contexts(libpath):
     budgeted = serve.serving_config()
     assert g.gp_voxels_query_sizes(budgeted) <= budgeted.mem_budget
     assert g.gp_voxels_query_sizes(budgeted) > budgeted.mem_budget - 16 * mb
+    # with the voxel state machine on, the scan slots keep the CUDA-core variance and the
+    # batch entry gets the whole workspace (capped by what max_voxels voxels could use)
+    fb = dict(mem_budget=0, eta=0.3, noise_floor=4e-6)
+    on = g.gp_voxels_query_sizes(serve.serving_config(**fb))
+    off = g.gp_voxels_query_sizes(serve.serving_config(tc_workspace_mb=0, **fb))
+    assert 4095 * mb < on - off <= 4096 * mb + (1 << 16) * 24 + 4096
