@@ -126,6 +126,11 @@ typedef struct {
                             dropped.  A call whose eligible voxels need more than its share
                             forms every variance on the CUDA cores instead, so the choice
                             never depends on scheduling.  0 turns it off; default 4096. */
+    int refine;          /* GPV_PREC_FP32 solves: 1 (default) adds one step of iterative
+                            refinement of alpha = (K + sigma^2 I)^-1 (f - m): the residual
+                            r = (f - m) - (K + sigma^2 I) alpha is accumulated in float-float,
+                            the FP32 factor solves for the correction, and the mean of Eq. 3
+                            is accumulated in float-float; 0: plain FP32 throughout */
 } gp_voxels_config;
 
 /* Voxel types of Sec. 3.3 (gp_voxels_scan_types, gp_voxels_type_counts). */
@@ -377,8 +382,10 @@ GPV_API int gp_voxels_store_voxels(gp_voxels_t* h, int64_t* h_voxels);
  *  - Voxels whose factor does not fit shared memory (in FP32 about 256 points at
  *    G <= 16; in the 8-byte precisions about 176) are not solved and get
  *    GPV_VOX_TOO_LARGE; gp_voxels_solve_csr handles them.
- *  - The first call on a device looks up the scratch area's device address; make that
- *    first call before capturing a stream.
+ *  - The first call on a device looks up the scratch area's device address (again after
+ *    the device's context has been replaced, e.g. by cudaDeviceReset); make that first
+ *    call before capturing a stream.
+ *  - cfg->factor_panel must be 0, 4, 8 or 16, as for gp_voxels_create.
  *  - All calls share the scratch area: calls whose GPU work overlaps (on different
  *    streams, or from several threads) race and give wrong results.  Serialise them.
  *  - No cudaMalloc, cudaFree or other allocating call is made.

@@ -157,6 +157,7 @@ static int validate(const gp_voxels_config* c)
     if (c->init_mode < 0 || c->init_mode > 1) return GPV_EINVAL;
     if (!(c->esc_cond > 1.f)) return GPV_EINVAL;
     if (c->tc_workspace_mb < 0 || c->tc_workspace_mb > (1 << 20)) return GPV_EINVAL;
+    if (c->refine < 0 || c->refine > 1) return GPV_EINVAL;
     if (c->factor_panel != 0 && c->factor_panel != 4 && c->factor_panel != 8 && c->factor_panel != 16)
         return GPV_EINVAL;
     if (c->hash_capacity & (c->hash_capacity - 1)) return GPV_EINVAL;
@@ -286,6 +287,7 @@ extern "C" int gp_voxels_config_default(gp_voxels_config* c)
     c->sf2 = 1.f;
     c->sn2 = 4e-4f;
     c->tc_workspace_mb = 4096;
+    c->refine = 1;
     return GPV_OK;
 }
 
@@ -547,6 +549,7 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     a.tau = c.tau; a.mean_mode = c.mean_mode; a.init_mode = c.init_mode;
     a.esc_cond = c.esc_cond;
     a.escalate = kind == PREC_FF ? 1 : 0;
+    a.refine = kind == PREC_F32 ? c.refine : 0;
     a.axis = d_axis; a.mean = d_mean; a.var = d_var; a.status = d_status;
     a.pos = d_pos; a.scale = d_scale; a.quat = d_quat;
     a.noise = d_noise; a.pvar = d_pvar; a.skip = d_skip;

@@ -52,6 +52,7 @@ struct SolveArgs {
     float esc_cond;
     int escalate;        // 1: badly conditioned voxels go to esc_list instead of being solved
     int escalation_pass; // 1: this launch re-solves escalated voxels (sets VOX_ESCALATED)
+    int refine;          // FP32: one step of iterative refinement of alpha (float-float residual)
     // outputs
     uint8_t* axis;
     float* mean;

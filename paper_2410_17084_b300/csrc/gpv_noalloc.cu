@@ -12,8 +12,10 @@
 // counters, the voxel work list and the escalation lists).  Here that scratch is one
 // file-scope __device__ array of fixed size: it exists on every GPU that loads the
 // library, for the life of the process, and every call shares it.  Its device address is
-// taken once per device with cudaGetSymbolAddress (host code cannot use the array's name
-// as a pointer: on the host that name is only a stand-in).  The counters that must start
+// taken with cudaGetSymbolAddress once per device and context, by the first call on a
+// device (which should therefore come before any stream capture) and again after that
+// device's context has been replaced (host code cannot use the array's name as a
+// pointer: on the host that name is only a stand-in).  The counters that must start
 // at zero are cleared on the stream at the start of every call.
 //
 // Limits: at most kNoAllocMaxVoxels voxels per call; voxels whose factor does not fit
@@ -50,7 +52,31 @@ static_assert(kOffEscCount + 2 <= kOffWork, "scratch header overflows");
 static __device__ __align__(256) int32_t g_noalloc_scratch[kScratchInts];
 
 std::mutex g_mu;
-int32_t* g_scratch_ptr[kMaxDevices] = {};
+// per device: the scratch array's address and the context it was taken in.  A context
+// that is destroyed and created again (cudaDeviceReset, a primary context released by its
+// last user) reloads the module, and the array may then sit elsewhere, so the address is
+// looked up again whenever the device's current context is not the one it was taken in.
+struct ScratchAddr {
+    void* ctx = nullptr;
+    int32_t* ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
+
+// cuCtxGetCurrent, fetched through the runtime so that the library does not link the
+// driver library itself (it must load on machines without a GPU driver)
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(p);
+    }();
+    return fn;
+}
 
 struct Bounds {
     int hi[kNumBuckets];
@@ -68,21 +94,36 @@ int fail(cudaError_t e)
     return GPV_ECUDA;
 }
 
-// Device address of the scratch array on the current device (set-up on first use).
+// Device address of the scratch array on the current device: taken once per device and
+// context (the set-up of the first call on a device, or after its context changed).
 int scratch_on_current_device(int32_t** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(e);
     if (dev < 0 || dev >= kMaxDevices) return GPV_EINVAL;
+    CtxGetCurrentFn getc = ctx_get_current();
+    if (!getc) {
+        gpv_record_cuda_error(cudaErrorDeviceUninitialized);
+        return GPV_ECUDA;
+    }
+    void* ctx = nullptr;
+    if (getc(&ctx) != 0) ctx = nullptr;  // null: no context is current yet
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchAddr& sa = g_scratch[dev];
+    if (!sa.ptr || !ctx || sa.ctx != ctx) {
+        // the lookup itself makes the device's primary context current where none was
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return fail(e);
-        g_scratch_ptr[dev] = static_cast<int32_t*>(p);
+        if (getc(&ctx) != 0 || !ctx) {
+            gpv_record_cuda_error(cudaErrorDeviceUninitialized);
+            return GPV_ECUDA;
+        }
+        sa.ptr = static_cast<int32_t*>(p);
+        sa.ctx = ctx;
     }
-    *out = g_scratch_ptr[dev];
+    *out = sa.ptr;
     return GPV_OK;
 }
 
@@ -106,7 +147,10 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
     if (!(c->voxel_size > 0.f) || c->grid_side < 1 || c->grid_side > kMaxG || c->n_s < 1 ||
         c->n_r < 1 || c->n_s * c->n_r != c->grid_side || c->tau < 1 ||
         c->max_points < c->tau || c->mean_mode < 0 || c->mean_mode > 1 || c->precision < 0 ||
-        c->precision > 2 || c->init_mode < 0 || c->init_mode > 1 || !(c->esc_cond > 1.f))
+        c->precision > 2 || c->init_mode < 0 || c->init_mode > 1 || !(c->esc_cond > 1.f) ||
+        c->refine < 0 || c->refine > 1)
+        return GPV_EINVAL;
+    if (c->factor_panel != 0 && c->factor_panel != 4 && c->factor_panel != 8 && c->factor_panel != 16)
         return GPV_EINVAL;
     if (nvox == 0) return GPV_OK;
     if (!d_xyz || !d_offsets || !d_centres || !d_lambda || !d_sf2 || !d_sn2 || !d_axis ||
@@ -152,6 +196,7 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
     a.tau = c->tau; a.mean_mode = c->mean_mode; a.init_mode = c->init_mode;
     a.esc_cond = c->esc_cond;
     a.escalate = kind == PREC_FF ? 1 : 0;
+    a.refine = kind == PREC_F32 ? c->refine : 0;
     a.axis = d_axis; a.mean = d_mean; a.var = d_var; a.status = d_status;
     a.pos = d_pos; a.scale = d_scale; a.quat = d_quat;
     a.esc_list = scr + kOffEsc; a.esc_count = scr + kOffEscCount;
@@ -178,7 +223,9 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
         a.work_count = scr + kOffCount + b;
         a.work_next = scr + kOffNext + b;
         a.nmax = bnd.hi[b];
-        a.percol_max = bnd.hi[b] <= default_percol_max(kind == PREC_F32 ? 4 : 8) ? bnd.hi[b] : 0;
+        // an explicit panel width selects the blocked factor for every bucket
+        a.percol_max = c->factor_panel == 0 && bnd.hi[b] <= default_percol_max(kind == PREC_F32 ? 4 : 8)
+                           ? bnd.hi[b] : 0;
         if ((e = launch_solve(kind, true, nt, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
     }
     if (kind == PREC_FF) {  // FP64 re-solve of the voxels that failed the conditioning check
@@ -195,6 +242,7 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
         a.work_next = scr + kOffNext + nb;
         a.nmax = a.nmax_small_f64;
         a.percol_max = default_percol_max(8);
+        a.panel = 16;  // the escalation pass of the handle path uses 16-column panels
         if ((e = launch_solve(PREC_F64, true, nt, a, sms * occ, smem, s)) != cudaSuccess) return fail(e);
     }
     return GPV_OK;

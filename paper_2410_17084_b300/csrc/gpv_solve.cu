@@ -884,6 +884,47 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         al[i] = (acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3]));
     }
 
+    // ---- A5': one step of iterative refinement of alpha (FP32 path) -----------------
+    // r = (f - m) - (K + D) alpha: K recomputed as in A3, every product exact (FMA) and
+    // the sum in float-float, so r carries the factor's error rather than the rounding
+    // of the sum; the FP32 inverse factor then gives the correction d = X^T X r, and the
+    // mean below accumulates K*^T (alpha + d) in float-float.  (tmp is free once alpha
+    // is formed, and f - m once r is.)
+    const bool refine = sizeof(T) == 4 && A.refine != 0;
+    T* dal = tmp;  // the correction d, when refining
+    if (refine) {
+        __syncthreads();
+        for (int j = tid; j < n; j += nthr) {
+            const float xj1 = to_f(x1[j]), xj2 = to_f(x2[j]);
+            float sh = to_f(fv[j]), sl = 0.f;
+            for (int i = 0; i < n; ++i) {
+                const float d1 = __fsub_rn(xj1, to_f(x1[i])), d2 = __fsub_rn(xj2, to_f(x2[i]));
+                float k = to_f(sf2 * gexpw(nlam * (d1 * d1 + d2 * d2), xtab));
+                if (i == j) k = __fadd_rn(k, A.noise ? __ldg(A.noise + beg + j) : sn2f);
+                const float a = to_f(al[i]);
+                const float p = __fmul_rn(k, a), pe = __fmaf_rn(k, a, -p);
+                const ff t = two_sum(sh, -p);
+                sh = t.hi;
+                sl = __fadd_rn(sl, __fsub_rn(t.lo, pe));
+            }
+            tmp[j] = from_f<T>(__fadd_rn(sh, sl));
+        }
+        __syncthreads();
+        for (int j = tid; j < n; j += nthr) {  // X r
+            T s2 = zero<T>();
+            for (int i = 0; i <= j; ++i) acc_fma(s2, L[tri_off(i, n) + (j - i)], tmp[i]);
+            fv[j] = acc_norm(s2);
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += nthr) {  // X^T (X r)
+            T s2 = zero<T>();
+            const T* col = L + tri_off(i, n) - i;
+            for (int j = i; j < n; ++j) acc_fma(s2, col[j], fv[j]);
+            dal[i] = acc_norm(s2);
+        }
+        __syncthreads();
+    }
+
     // ---- A8 handed over: L^-1 and the factors go to the workspace, k_var_tc forms the
     // variance on the tensor cores ------------------------------------------------------
     const int ntri = n * (n + 1) / 2;
@@ -990,7 +1031,15 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
             for (int w = 0; w < 4; ++w)
                 acc_fma(s4[w], al[i + w] * fa[(i + w) * G + u], fb[(i + w) * Gp + vv]);
         for (; i < n; ++i) acc_fma(s4[0], al[i] * fa[i * G + u], fb[i * Gp + vv]);
-        const T mu = m + ((acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3])));
+        T mu = m + ((acc_norm(s4[0]) + acc_norm(s4[1])) + (acc_norm(s4[2]) + acc_norm(s4[3])));
+        if (refine) {  // m + K*^T (alpha + d), float-float sum of FP32 kernel values
+            ff acc = ff_make(0.f, 0.f);
+            for (int i = 0; i < n; ++i) {
+                const float k = __fmul_rn(to_f(fa[i * G + u]), to_f(fb[i * Gp + vv]));
+                acc_fma(acc, ff_make(k, 0.f), two_sum(to_f(al[i]), to_f(dal[i])));
+            }
+            mu = from_f<T>(to_f(ff_make(to_f(m), 0.f) + acc_norm(acc)));
+        }
         if (tc) {
             A.mean[obase + q] = to_f(mu);
             Wtc[ntri + n * G + n * Gp + q] = mu;

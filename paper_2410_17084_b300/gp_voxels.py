@@ -62,6 +62,7 @@ class gp_voxels_config(ctypes.Structure):
         ("noise_floor", ctypes.c_float),
         ("factor_panel", ctypes.c_int),
         ("tc_workspace_mb", ctypes.c_int),
+        ("refine", ctypes.c_int),
     ]
 
 

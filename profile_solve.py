@@ -1,6 +1,6 @@
 """Run one batched solve on a prefix of a synthetic workload, for profilers (ncu).
 
-    python -m paper_2410_17084_b300.profile_solve --nvox 10000 --precision 1
+    python profile_solve.py --nvox 10000 --precision 1
 
 prints the CUDA-event time of each repetition.  Workloads: quadric (the bench workload),
 mixed (escalation workload), stress (1M-voxel workload), plane; with --path alg3 the
@@ -11,10 +11,14 @@ structure similarity loss of the workload's points against its initialised Gauss
 from __future__ import annotations
 
 import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 import torch
 
-from . import build, gp_voxels as gv, synth
+from paper_2410_17084_b300 import build, gp_voxels as gv, synth
 
 
 def main():

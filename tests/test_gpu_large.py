@@ -1,0 +1,111 @@
+"""GPU parity of the large voxels against the FP64 oracle (GS-LIVM Sec. 3.1 Eq. 3): the
+shapes of the two biggest workloads, in every precision, element by element.
+
+  stress shapes: power-law counts on [4, 1024], G = 9, voxels of 256..1024 points (the
+      factor does not fit shared memory);
+  escalation-workload shapes: power-law counts on [32, 512], G = 32 (eight 128-query
+      tiles per voxel), well-conditioned voxels (the collinear ones are covered by the
+      escalation test of the mixed path).
+
+Tolerances: mixed and FP64 paths as everywhere (mean 1e-4 m, variance 1e-3 relative
+against max(var_ref, 1e-3 sigma^2)).  Plain FP32 path with one step of refinement of
+alpha: mean 1e-4 m; its variance carries the FP32 rounding of the kernel values, about
+eps_32 |w|^2 relative (w the kriging weights), and is held to FP32_VAR_TOL.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+MEAN_TOL = 1e-4
+VAR_TOL = 1e-3
+FP32_MEAN_TOL = 1e-4
+FP32_VAR_TOL = 0.25
+
+
+@pytest.fixture(scope="module")
+def gpv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_17084_b300 import build, gp_voxels
+    build.build()
+    return gp_voxels
+
+
+def _run(gpv, b, precision, **kw):
+    import torch
+    d = dict(voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau,
+             max_points=int(max(b.counts.max(), b.tau, 8)), max_voxels=max(b.nvox, 1),
+             precision=precision, mean_mode=1)
+    d.update(kw)
+    g = gpv.GpVoxels(gpv.gp_voxels_config_default(**d))
+    dv = gpv.batch_to_device(b)
+    out = g.solve_csr(dv["xyz"], dv["offsets"], dv["centres"], dv["lam"], dv["sf2"], dv["sn2"])
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    g.close()
+    return res
+
+
+def _check(b, out, mean_tol, var_tol, name):
+    from oracle import compare
+    ref = compare.oracle_for_batch(b, gpu_axis=out["axis"].astype(np.int32))
+    solved = ref["status"] == 0
+    ok_gpu = (out["status"].astype(np.uint32) & 0x55) == 0
+    assert np.array_equal(solved, ok_gpu), f"{name}: solved masks differ"
+    err = compare.gpr_errors(out["mean"], out["var"], ref, b.sn2, solved)
+    print(f"\n{name}: n={b.counts.min()}..{b.counts.max()} {err}")
+    assert err["mean_max"] <= mean_tol, f"{name}: mean error {err['mean_max']}"
+    assert err["var_max"] <= var_tol, f"{name}: variance error {err['var_max']}"
+    return err
+
+
+def _stress_large(nsel=24, seed=4):
+    """The largest voxels of a 60,000-voxel stress batch, spread over 256..1024 points."""
+    from paper_2410_17084_b300 import synth
+    full = synth.stress_batch(60000, seed=seed)
+    big = np.nonzero(full.counts >= 256)[0]
+    order = big[np.argsort(full.counts[big])]
+    pick = order[np.linspace(0, order.size - 1, nsel).astype(int)]
+    return full.subset(np.unique(pick))
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_stress_large_voxels(gpv, oracle, precision):
+    b = _stress_large()
+    assert b.counts.max() >= 1000 and b.counts.min() >= 256
+    out = _run(gpv, b, precision)
+    mt, vt = (FP32_MEAN_TOL, FP32_VAR_TOL) if precision == 0 else (MEAN_TOL, VAR_TOL)
+    _check(b, out, mt, vt, f"stress-large prec={precision}")
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_escalation_shapes_g32(gpv, oracle, precision):
+    """G = 32 with counts over the whole 32..512 range, including the largest."""
+    from paper_2410_17084_b300 import synth
+    full = synth.mixed_batch(4000, seed=7)
+    good = np.nonzero(~full.degenerate)[0]
+    order = good[np.argsort(full.counts[good])]
+    idx = np.unique(np.concatenate([order[-16:], order[:: max(1, order.size // 48)]]))
+    b = full.subset(idx)
+    assert b.counts.max() > 400
+    out = _run(gpv, b, precision)
+    mt, vt = (FP32_MEAN_TOL, FP32_VAR_TOL) if precision == 0 else (MEAN_TOL, VAR_TOL)
+    _check(b, out, mt, vt, f"escalation-shapes G=32 prec={precision}")
+
+
+def test_fp32_refinement_helps(gpv, oracle):
+    """The refinement step of alpha lowers the FP32 mean error (C2 shapes)."""
+    from oracle import compare
+    from paper_2410_17084_b300 import synth
+    full = synth.quadric_batch(3000, seed=9)
+    b = full.subset(np.arange(800))
+    errs = {}
+    for r in (0, 1):
+        out = _run(gpv, b, 0, refine=r)
+        ref = compare.oracle_for_batch(b, gpu_axis=out["axis"].astype(np.int32))
+        errs[r] = compare.gpr_errors(out["mean"], out["var"], ref, b.sn2, ref["status"] == 0)
+    print(f"\nfp32 plain {errs[0]}\nfp32 refined {errs[1]}")
+    assert errs[1]["mean_max"] <= FP32_MEAN_TOL
+    assert errs[1]["mean_max"] < errs[0]["mean_max"]

@@ -8,8 +8,8 @@ static scratch area of the library instead.  Two calls in a row must both match 
 handle path (the second one sees the scratch left by the first), within the tolerance of
 the other parity tests: posterior mean 1e-4 m, variance 1e-3 relative.
 
-This file is collected last on purpose, so a failure here stops a run only after every
-other test has run.
+The file is named to be collected after the other GPU tests; it passes alone in a fresh
+process as well as after them (the static scratch keeps whatever earlier calls left).
 """
 import numpy as np
 import pytest
@@ -27,8 +27,8 @@ def _batch():
     return full.subset(keep)
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_noalloc_matches_handle_solve_twice(precision):
+@pytest.mark.parametrize("precision,panel", [(1, 0), (0, 0), (1, 8)])
+def test_noalloc_matches_handle_solve_twice(precision, panel):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -38,7 +38,7 @@ def test_noalloc_matches_handle_solve_twice(precision):
     d = gv.batch_to_device(b)
     cfg = gv.gp_voxels_config_default(voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r,
                                       tau=b.tau, max_points=160, max_voxels=b.nvox,
-                                      precision=precision)
+                                      precision=precision, factor_panel=panel)
     g = gv.GpVoxels(cfg)
     ref = g.solve_csr(d["xyz"], d["offsets"], d["centres"], d["lam"], d["sf2"], d["sn2"],
                       init=True)
@@ -84,6 +84,12 @@ def test_noalloc_limits():
     off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
     with pytest.raises(gv.GpvError) as ei:
         gv.gp_voxels_solve_csr_noalloc(cfg, z, off, n, z, z, z, z, z, z, z, z)
+    assert ei.value.code == gv.GPV_EINVAL
+    # a panel width the handle path rejects is rejected here too
+    bad = gv.gp_voxels_config_default(voxel_size=0.5, grid_side=16, n_s=4, n_r=4, tau=16,
+                                      max_points=256, precision=gv.PREC_MIXED, factor_panel=5)
+    with pytest.raises(gv.GpvError) as ei:
+        gv.gp_voxels_solve_csr_noalloc(bad, z, off, 1, z, z, z, z, z, z, z, z)
     assert ei.value.code == gv.GPV_EINVAL
     # a voxel too large for shared memory is reported, not solved
     b = synth.quadric_batch(50, seed=32)
