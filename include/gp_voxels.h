@@ -131,6 +131,12 @@ typedef struct {
                             r = (f - m) - (K + sigma^2 I) alpha is accumulated in float-float,
                             the FP32 factor solves for the correction, and the mean of Eq. 3
                             is accumulated in float-float; 0: plain FP32 throughout */
+    int tall_min_points; /* GPV_PREC_MIXED and GPV_PREC_FP32 batch solves: voxels with more
+                            points than this take the tensor-core factorisation of the tall
+                            matrix [K + sigma^2 I; K*^T] (left-looking Cholesky whose
+                            updates are exact BF16 slice products; no L^-1); 0 (default):
+                            every voxel too large for the shared-memory kernels; -1: off
+                            (those voxels keep the global-workspace kernel) */
 } gp_voxels_config;
 
 /* Voxel types of Sec. 3.3 (gp_voxels_scan_types, gp_voxels_type_counts). */

@@ -50,6 +50,7 @@ struct Bucket {
     bool tri_smem; // factor in shared memory (else in the global workspace slice)
     bool percol;   // per-column (not blocked) factor and inverse
     int panel;     // panel width of the blocked factor (4, 8, 16)
+    bool tall;     // the bucket's voxels take the tall-matrix tensor-core factorisation
     bool tcv_ok;   // float-float bucket whose voxels all take the tensor-core variance
     VarCfg v;      // its launch configuration in that case
 };
@@ -86,6 +87,7 @@ struct SolveCtx {
     int32_t* d_tc_fb = nullptr;
     long long* d_tc_off_v = nullptr;  // per row
     int32_t* d_tc_next = nullptr;     // k_var_tc dequeue counter per size bucket
+    unsigned char* d_tall = nullptr;  // slice stores of the tall-matrix factorisation (one per CTA)
     cudaStream_t side[kNumBuckets] = {};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[kNumBuckets] = {};
@@ -104,6 +106,8 @@ struct gp_voxels {
     int32_t* d_pl_next = nullptr;   // max_voxels counters (one-per-launch baseline)
     int64_t gws_stride = 0;         // elements (8-byte) per slice
     int gws_grid = 0;
+    int tall_min = INT_MAX;         // voxels with more points take the tall-matrix path
+    int64_t tall_stride = 0;        // bytes of one CTA's slice store
     int esc_grid_small = 0, esc_smem_small = 0, esc_grid_big = 0, esc_smem_big = 0;
     size_t bytes = 0;
     gpv_store* store = nullptr;
@@ -158,6 +162,7 @@ static int validate(const gp_voxels_config* c)
     if (!(c->esc_cond > 1.f)) return GPV_EINVAL;
     if (c->tc_workspace_mb < 0 || c->tc_workspace_mb > (1 << 20)) return GPV_EINVAL;
     if (c->refine < 0 || c->refine > 1) return GPV_EINVAL;
+    if (c->tall_min_points < -1 || c->tall_min_points > 1024) return GPV_EINVAL;
     if (c->factor_panel != 0 && c->factor_panel != 4 && c->factor_panel != 8 && c->factor_panel != 16)
         return GPV_EINVAL;
     if (c->hash_capacity & (c->hash_capacity - 1)) return GPV_EINVAL;
@@ -207,7 +212,13 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         P.tc_nmax = std::min(std::min(kTcMaxN, c.max_points), std::max(nmax_tcv, P.nmax_smem));
         P.tc_nmax_gl = std::min(kTcMaxNGl, c.max_points);
     }
+    const bool tall_on = kind == prec_kind(c.precision) && h->tall_min != INT_MAX;
     std::vector<int> bounds = bucket_bounds(c.max_points, P.nmax_smem, P.tc_nmax);
+    if (tall_on && std::find(bounds.begin(), bounds.end(), h->tall_min) == bounds.end()) {
+        bounds.push_back(h->tall_min);
+        std::sort(bounds.begin(), bounds.end());
+        while ((int)bounds.size() > kNumBuckets) bounds.erase(bounds.begin());
+    }
     P.nb = (int)bounds.size();
     int hi_host[kNumBuckets];
     for (int i = 0; i < P.nb; ++i) {
@@ -229,11 +240,12 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         if (occ < 1) return GPV_EINVAL;
         B.grid = B.tri_smem ? h->sms * occ : h->gws_grid;
         B.tcv_ok = false;
+        B.tall = tall_on && B.hi > h->tall_min;
     }
     if (tc_on) {  // the variant for every bucket up to its largest n (shared memory)
         for (int i = 0; i < P.nb; ++i) {
             Bucket& B = P.b[i];
-            if (B.hi > P.tc_nmax) continue;
+            if (B.hi > P.tc_nmax || B.tall) continue;
             B.tcv_ok = true;
             // defaults as the autotuner picks them on the quadric workload: without the
             // contraction, 256-thread CTAs (three per SM) beat 512 for blocked factors,
@@ -291,6 +303,34 @@ extern "C" int gp_voxels_config_default(gp_voxels_config* c)
     return GPV_OK;
 }
 
+// Smallest n that is not taken by the tall-matrix path: INT_MAX where the path is off
+// (FP64, tall_min_points = -1, or no voxel can exceed the threshold).  By default the
+// threshold is the largest n of the shared-memory kernels of the configured precision
+// (for the mixed precision with the tensor-core variance, the largest n of its
+// shared-memory variant), so the tall path replaces the global-workspace kernel.
+static int tall_threshold(const gp_voxels_config* c, int Gp)
+{
+    if (c->precision == GPV_PREC_FP64 || c->tall_min_points < 0) return INT_MAX;
+    int t = c->tall_min_points;
+    if (t == 0) {
+        const int kind = c->precision == GPV_PREC_FP32 ? PREC_F32 : PREC_FF;
+        int nsm = 0, ntcv = 0;
+        if (solve_max_smem_n(kind, c->grid_side, Gp, &nsm) != cudaSuccess) return INT_MAX;
+        t = nsm;
+        if (kind == PREC_FF && c->tc_workspace_mb > 0 &&
+            solve_max_smem_n(kind, c->grid_side, Gp, &ntcv, true) == cudaSuccess)
+            t = std::max(t, std::min(kTcMaxN, ntcv));
+    }
+    return t < c->max_points ? t : INT_MAX;
+}
+
+static size_t tall_bytes(const gp_voxels_config* c, int sms, int Gp)
+{
+    if (tall_threshold(c, Gp) == INT_MAX) return 0;
+    const int kind = c->precision == GPV_PREC_FP32 ? PREC_F32 : PREC_FF;
+    return (size_t)sms * (size_t)tall_ws_stride(kind, c->max_points, c->grid_side);
+}
+
 static size_t ctx_bytes(const gp_voxels_config* c, int cap, int sms, int Gp)
 {
     size_t b = 4 * sizeof(int32_t) * (kNumBuckets + 2) + 2 * sizeof(int32_t);
@@ -341,6 +381,7 @@ static TcSplit tc_split(const gp_voxels_config* c, int Gp, size_t rest)
 static size_t solve_bytes(const gp_voxels_config* c, int sms, int Gp)
 {
     size_t b = ctx_bytes(c, c->max_voxels, sms, Gp);
+    b += tall_bytes(c, sms, Gp);
     b += sizeof(int32_t) * ((size_t)c->max_voxels * 2 + 1);  // ident, per-launch counters
     if (c->hash_capacity > 0)
         b += (size_t)c->scan_slots * ctx_bytes(c, c->max_scan_voxels, sms, Gp);
@@ -369,7 +410,7 @@ static void ctx_release(SolveCtx& x)
     cudaFree(x.d_bcount); cudaFree(x.d_bbase); cudaFree(x.d_bcursor); cudaFree(x.d_next);
     cudaFree(x.d_work); cudaFree(x.d_esc_list); cudaFree(x.d_esc_count); cudaFree(x.d_gws);
     cudaFree(x.d_tc_ws); cudaFree(x.d_tc); cudaFree(x.d_tc_v); cudaFree(x.d_tc_off); cudaFree(x.d_tc_fb);
-    cudaFree(x.d_tc_off_v); cudaFree(x.d_tc_next);
+    cudaFree(x.d_tc_off_v); cudaFree(x.d_tc_next); cudaFree(x.d_tall);
     for (int i = 0; i < kNumBuckets; ++i) {
         if (x.side[i]) cudaStreamDestroy(x.side[i]);
         if (x.ev_join[i]) cudaEventDestroy(x.ev_join[i]);
@@ -471,6 +512,22 @@ static int create_impl(gp_voxels_t* h)
 #undef AL
     h->gws_stride = gws_slice_elems(c.max_points, c.grid_side, h->Gp);
     if ((rc = ctx_create(h, h->main, c.max_voxels, need_tc.main)) != GPV_OK) return rc;
+    h->tall_min = tall_threshold(&c, h->Gp);
+    if (h->tall_min != INT_MAX) {
+        const int kind = prec_kind(c.precision);
+        const int np = (c.max_points + 31) / 32 * 32;
+        int dev = 0, optin = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (tall_smem(kind, np) + 8192 > optin) return GPV_EINVAL;  // max_points too large
+        CK(tall_prepare(kind, np));
+        h->tall_stride = tall_ws_stride(kind, c.max_points, c.grid_side);
+        const size_t b = (size_t)h->sms * (size_t)h->tall_stride;
+        cudaError_t e = cudaMalloc((void**)&h->main.d_tall, b);
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return GPV_ENOMEM; }
+        if (e != cudaSuccess) return cuda_fail(e);
+        h->bytes += b;
+    }
     if (need_tc.main > 0 || (c.hash_capacity > 0 && need_tc.slot > 0)) CK(var_tc_prepare());
     if (c.hash_capacity > 0) {
         h->sctx = new (std::nothrow) SolveCtx[c.scan_slots];
@@ -639,7 +696,9 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_count = x.d_bcount + b;
         a.work_next = x.d_next + b;
         a.nmax = (B.tri_smem || tcv) ? B.hi : c.max_points;
-        if (tcv) {  // the variance goes to the tensor cores
+        if (B.tall && x.d_tall && !a.pvar) {  // large voxels: the tall-matrix factorisation
+            CK(launch_tall(kind, a, x.d_tall, h->tall_stride, (B.hi + 31) / 32 * 32, h->sms, ss));
+        } else if (tcv) {  // the variance goes to the tensor cores
             a.percol_max = B.v.percol ? B.hi : 0;
             a.panel = B.v.panel;
             CK(launch_solve(kind, true, B.v.nthr, a, B.v.grid, B.v.smem, ss, true));
@@ -1123,6 +1182,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
     const int cand[3] = {128, 256, 512};
     for (int b = 0; b < P.nb; ++b) {
         Bucket& B = P.b[b];
+        if (B.tall && h->main.d_tall) continue;  // one launch shape: one CTA of 384 threads per SM
         const bool tcv = a.tc_ws && B.tcv_ok;  // tune the variant the batch entry launches
         const bool tri = B.tri_smem || tcv;     // its factor is in shared memory
         float best_ms = 3.0e38f;

@@ -215,6 +215,15 @@ cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out, bool tcv = 
 cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int* blocks_per_sm,
                             bool tcv = false);
 cudaError_t launch_var_tc(const SolveArgs& a, int sms, cudaStream_t s);
+// Large voxels: blocked Cholesky of the tall matrix [K + D; K*^T] on the tensor cores
+// (gpv_tall.cu).  prec PREC_FF (six BF16 slices) or PREC_F32 (three); npmax = largest n
+// of the launch rounded up to 32; ws holds one slice store of tall_ws_stride() bytes per
+// CTA; grid = CTAs (one per SM).
+int tall_smem(int prec, int npmax);
+int64_t tall_ws_stride(int prec, int nmax, int G);
+cudaError_t tall_prepare(int prec, int npmax);
+cudaError_t launch_tall(int prec, const SolveArgs& a, unsigned char* ws, int64_t ws_stride, int npmax,
+                        int grid, cudaStream_t s);
 cudaError_t launch_init_tc(const SolveArgs& a, int sms, cudaStream_t s);
 cudaError_t var_tc_prepare();
 cudaError_t launch_init(const float* mean, const float* var, const uint8_t* axis,

@@ -1,0 +1,678 @@
+// gpv_tall.cu -- Voxel-GPR of large voxels (GS-LIVM Sec. 3.1, Alg. 1, Eq. 2-3) as one
+// blocked Cholesky of a tall matrix whose trailing updates run on the fifth-generation
+// tensor cores (tcgen05) as exact BF16 slice products.
+//
+// The matrix.  For a voxel of n points (padded to np, a multiple of 32, by identity rows)
+// and Q = G^2 query nodes, the rows of
+//          M = [ K + D ]   np x np, lower triangle   (Gram + noise, Eq. 2)
+//              [ K*^T  ]   Q  x np                    (cross-covariance, Eq. 2)
+// are factored through their first np columns: rows 0..np-1 become L (K + D = L L^T) and
+// the query rows become V = K*^T L^-T, so that
+//          var_q = sf2 - |V_q|^2     and     mu_q = m + V_q . z,   z = L^-1 (f - m)
+// (Eq. 3, diagonal of Sigma* only).  Neither L^-1 nor the full Sigma* of the paper's
+// Alg. 3 is formed: the explicit inverse is n^3/3 flops the method does not need, which
+// at G = 9 is more than the triangular solve it would replace.
+//
+// The factor (left-looking, panels of 32 columns).  Panel p (columns c0 = 32 p ..
+// c0 + 31) of every row r >= c0 is
+//          P[r, :] = M[r, panel] - sum_{k < c0} L[r, k] L[panel, k]
+// a GEMM of the rows (M tiles of 128) against the panel's own rows (N = 32) over all
+// earlier columns, which the tensor cores do; then the 32 x 32 diagonal block is factored
+// (one warp, float-float), every row solves against it (L[r, panel] = P[r, :] L_pp^-T),
+// z is extended by forward substitution, and each query row adds its new entries to the
+// running sums |V_q|^2 and V_q . z.  Original entries of M are recomputed when a panel
+// needs them (kernel values from the points, K* from the separable node factors).
+//
+// Precision.  Each finished entry of L and V is cut into NSL slices of 8 bits on a
+// power-of-two grid fixed per row by a bound on the row's norm (Gram row r:
+// |L_r|^2 = A_rr; query row: |V_q|^2 = sf2 - var_q <= sf2), the scheme of Ozaki, Ogita,
+// Oishi and Rump (Numer. Algorithms 59, 2012).  A slice is exactly a BF16 number and a
+// product of two slices is exact in FP32.  The products of one level l = s + t share one
+// grid, and level l has its own FP32 accumulator in tensor memory: by Cauchy-Schwarz
+// over the row norms, level 0 stays below 2^14 grid units and level 1 below 2^20 for any
+// K; the levels of remainder slices (products of up to 2^14 units, signs close to
+// random) grow like sqrt(K) 2^14 / 3 (2^17.4 at K = 1024, against 2^24 for exactness).
+// The mixed path uses NSL = 6 (48 bits, 21 products per element); the FP32 path NSL = 3
+// (24 bits, 6 products).  Pairs with s + t >= NSL are dropped (below 2^-8 NSL of the row
+// scale).  The diagonal-block factor, the solves against it and the running sums are in
+// the working type (float-float or FP32) on the CUDA cores.
+//
+// Organisation.  One persistent CTA per SM (384 threads) takes the voxels of a size
+// bucket, largest bucket first.  Warp 0 loads operand chunks (one 128 x 32 tile of each A
+// slice, one 32 x 32 tile of each B slice, contiguous in the slice store) with
+// cp.async.bulk into a ring of shared-memory stages, each completing on an mbarrier;
+// one thread of warp 1 issues the MMAs (M = 128, N = 32, K = 16, kind::f16) of a tile
+// into one of two accumulator sets (NSL levels x 32 columns each) and commits; warps
+// 4..7 and 8..11 take the even and odd tiles: they read the levels with tcgen05.ld (lane
+// = row), form P in the working type, solve, cut and store the slices.  Every wait is
+// bounded; a wait that gives up marks the voxel GPV_VOX_FAILED and the CTA stops.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gpv_common.cuh"
+#include "gpv_init.cuh"
+#include "gpv_internal.h"
+#include "gpv_num.cuh"
+#include "gpv_umma.cuh"
+
+namespace gpv {
+namespace {
+
+constexpr int kT = 384;        // threads per CTA
+constexpr int kBP = 32;        // panel width = MMA N
+constexpr int kMT = 128;       // rows per M tile
+constexpr int kNSt = 3;        // operand stages
+constexpr uint32_t kPolls = 1u << 26;
+constexpr int kSlA = kMT * kBP * 2;  // bytes of one slice of a 128 x 32 A tile
+constexpr int kSlB = kBP * kBP * 2;  // bytes of one slice of a 32 x 32 B tile
+constexpr int kGrpBytes = 512;       // one 8-row group of a 32-column panel slice
+
+template <int NSL> struct Plan {
+    static constexpr int stage = NSL * (kSlA + kSlB);
+    static constexpr int set_cols = NSL * kBP;  // tensor-memory columns of one set
+    static constexpr int tmem_cols = 2 * set_cols <= 256 ? 256 : 512;
+};
+
+// dynamic shared memory: [stages][x1, x2, y: np each][Lkk 32x32][rd 32][zp 32][Eg: np]
+__host__ __device__ inline int tall_smem_bytes(int nsl, int npmax, int tsize)
+{
+    int o = kNSt * nsl * (kSlA + kSlB);
+    o += 3 * npmax * tsize;
+    o += (kBP * kBP + 2 * kBP) * tsize;
+    o += 4 * npmax;
+    return (o + 15) & ~15;
+}
+
+// ---- small PTX wrappers -------------------------------------------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(umma::smem_addr(mbar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(umma::smem_addr(mbar)) : "memory");
+}
+// bulk copy global -> shared, completing bytes on the mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(umma::smem_addr(dst)), "l"(src), "r"(bytes), "r"(umma::smem_addr(mbar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count)
+{
+    asm volatile("bar.arrive %0, %1;" :: "r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float shfl_idx_t(float x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+__device__ __forceinline__ ff shfl_idx_t(ff x, int src)
+{
+    return ff_make(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
+}
+// x += y (y a float) with an unnormalised float-float accumulator
+__device__ __forceinline__ void add_f(float& x, float y) { x = __fadd_rn(x, y); }
+__device__ __forceinline__ void add_f(ff& x, float y)
+{
+    const ff s = two_sum(x.hi, y);
+    x.hi = s.hi;
+    x.lo = __fadd_rn(x.lo, s.lo);
+}
+__device__ __forceinline__ int vload(const int& x) { return *(const volatile int*)&x; }
+__device__ __forceinline__ void vstore(int& x, int y) { *(volatile int*)&x = y; }
+
+__device__ __forceinline__ float lo_of(float) { return 0.f; }
+__device__ __forceinline__ float lo_of(ff x) { return x.lo; }
+
+// Slices of x (|x| < 2^(E-1)) on the grids 2^(E-8), ..., 2^(E-8 NSL): round to the grid by
+// adding and subtracting 1.5 * 2^(grid exponent + 23), keep the exact remainder; the low
+// part of a float-float value joins the remainder after the third slice (that FP32 sum
+// errs by at most 2^(E-49)).  Returns the BF16 bit patterns (upper halves: every slice
+// has at most 8 significant bits).
+template <int NSL, class T>
+__device__ __forceinline__ void cut(T x, int E, uint32_t (&q)[NSL])
+{
+    float a = hi_of(x);
+    const float lo = lo_of(x);
+#pragma unroll
+    for (int s = 0; s < NSL; ++s) {
+        if (s == 3) a = __fadd_rn(a, lo);
+        const float sig = __uint_as_float(((uint32_t)(E - 8 * s + 15 + 127) << 23) | 0x400000u);
+        const float t = __fsub_rn(__fadd_rn(a, sig), sig);
+        a = __fsub_rn(a, t);
+        q[s] = __float_as_uint(t) >> 16;
+    }
+}
+
+// Byte offset of (panel p, slice s, 8-row group g) in the slice store; within it, row
+// r % 8 and column c (of the panel) sit at (c / 8) * 128 + (r % 8) * 16 + (c % 8) * 2:
+// core matrices of 8 rows x 16 bytes, K-major, so a 16-group A tile and a 4-group B tile
+// are contiguous and land in shared memory in the layout the MMA reads (LBO 128, SBO 512).
+__device__ __forceinline__ int64_t sl_off(int p, int s, int g, int nsl, int RG)
+{
+    return ((int64_t)(p * nsl + s) * RG + g) * kGrpBytes;
+}
+
+struct Sh {  // static shared state
+    uint64_t full[kNSt], empty[kNSt], acc_full[2], acc_empty[2];
+    uint32_t tmem;
+    int v, abort, broken, fail;
+    float dmin, dmax;
+    int axis;
+};
+
+}  // namespace
+
+// Workspace of one CTA: slice store, per-row running sums, node factors.
+__host__ __device__ inline int tall_np(int n) { return (n + kBP - 1) / kBP * kBP; }
+__host__ __device__ inline int tall_rg(int np, int Q) { return (np + Q + kMT + 7) / 8; }
+__host__ __device__ inline int64_t tall_ws_bytes(int nsl, int nmax, int G, int tsize)
+{
+    const int np = tall_np(nmax), Q = G * G;
+    const int64_t sl = (int64_t)(np / kBP) * nsl * tall_rg(np, Q) * kGrpBytes;
+    const int64_t rs = (int64_t)2 * (np + Q) * tsize;   // running sums w, s2 per row
+    const int64_t ab = (int64_t)2 * np * G * tsize;     // node factors a(u), b(v)
+    return (sl + rs + ab + 255) & ~(int64_t)255;
+}
+
+namespace {
+
+template <class T, int NSL>
+__global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, int64_t ws_stride,
+                                                int npmax)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ Sh sh;
+    __shared__ double red[6 * 32];
+    __shared__ T nodes[kMaxG];
+    __shared__ ff xtab[is_ff<T>::value ? 256 : 1];
+    using P = Plan<NSL>;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = A.G, Q = G * G;
+    unsigned char* wsb = ws + (int64_t)blockIdx.x * ws_stride;
+
+    T* x1 = reinterpret_cast<T*>(sm + kNSt * P::stage);
+    T* x2 = x1 + npmax;
+    T* yv = x2 + npmax;
+    T* Lkk = yv + npmax;       // 32 x 32, row-major
+    T* rd = Lkk + kBP * kBP;   // 1 / L_jj
+    T* zp = rd + kBP;          // z of the panel
+    int* Eg = reinterpret_cast<int*>(zp + kBP);
+
+    if (threadIdx.x < G)
+        nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
+                                       ((double)threadIdx.x + 0.5) * (double)A.size / (double)G);
+    if (is_ff<T>::value)
+        for (int i = tid; i < 256; i += kT) {
+            const double t = exp2((double)i / 256.0);
+            const float h = (float)t;
+            xtab[i] = ff_make(h, (float)(t - (double)h));
+        }
+    if (tid == 0) {
+        for (int i = 0; i < kNSt; ++i) { umma::mbar_init(&sh.full[i], 1); umma::mbar_init(&sh.empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { umma::mbar_init(&sh.acc_full[i], 1); umma::mbar_init(&sh.acc_empty[i], 4); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh.broken = 0;
+    }
+    if (warp == 2) umma::tmem_alloc(&sh.tmem, P::tmem_cols);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = sh.tmem;
+
+    // pipeline counters (each role keeps its own copy of the common schedule)
+    uint32_t cnt = 0;            // operand chunks (producer, MMA issuer)
+    uint32_t use[2] = {0, 0};    // tiles per accumulator set (MMA issuer, epilogue groups)
+    const uint32_t idesc = umma::idesc_bf16(kMT, kBP);
+
+    const int total = *A.work_count;
+    const int wbase = A.work_base ? *A.work_base : 0;
+    for (;;) {
+        if (tid == 0) {
+            const int i = atomicAdd(A.work_next, 1);
+            sh.v = i < total ? A.work[wbase + i] : -1;
+            sh.abort = 0;
+            sh.fail = 0;
+            sh.dmin = 3.0e38f;
+            sh.dmax = 0.f;
+        }
+        __syncthreads();
+        const int v = sh.v;
+        if (v < 0 || vload(sh.broken)) break;
+
+        // ---- A1/A2: points, value axis, local inputs and targets (all threads) ----------
+        const int64_t beg = A.offsets[v];
+        const int n = (int)(A.offsets[v + 1] - beg);
+        const int np = tall_np(n), NP = np / kBP, R = np + Q, RG = tall_rg(np, Q);
+        const float* src = A.xyz + 3 * beg;
+        const float cx = A.centres[3 * v + 0], cy = A.centres[3 * v + 1], cz = A.centres[3 * v + 2];
+        {
+            float* redf = reinterpret_cast<float*>(red);
+            float s3[3] = {0.f, 0.f, 0.f};
+            for (int i = tid; i < n; i += kT) {
+                s3[0] += __ldg(src + 3 * i) - cx;
+                s3[1] += __ldg(src + 3 * i + 1) - cy;
+                s3[2] += __ldg(src + 3 * i + 2) - cz;
+            }
+            block_sum<float, 3>(s3, redf);
+            const float inv_n = 1.f / (float)n;
+            const float m0 = s3[0] * inv_n, m1 = s3[1] * inv_n, m2 = s3[2] * inv_n;
+            float c6[6] = {0, 0, 0, 0, 0, 0};
+            for (int i = tid; i < n; i += kT) {
+                const float d0 = (__ldg(src + 3 * i) - cx) - m0;
+                const float d1 = (__ldg(src + 3 * i + 1) - cy) - m1;
+                const float d2 = (__ldg(src + 3 * i + 2) - cz) - m2;
+                c6[0] += d0 * d0; c6[1] += d0 * d1; c6[2] += d0 * d2;
+                c6[3] += d1 * d1; c6[4] += d1 * d2; c6[5] += d2 * d2;
+            }
+            block_sum<float, 6>(c6, redf);
+            if (tid == 0) sh.axis = value_axis_from_cov(c6);
+            __syncthreads();
+        }
+        const int axis = sh.axis;
+        const int pa1 = axis == 2 ? 0 : axis + 1;
+        const int pa2 = axis == 0 ? 2 : (axis == 1 ? 0 : 1);
+        const float cen[3] = {cx, cy, cz};
+        const float lamf = A.lam[v], sf2f = A.sf2[v], sn2f = A.sn2[v];
+        const T nlam = from_f<T>(-lamf), sf2 = from_f<T>(sf2f);
+        T msum[1] = {zero<T>()};
+        float nmin = 3.0e38f;
+        for (int i = tid; i < np; i += kT) {
+            if (i < n) {
+                x1[i] = diff_f<T>(__ldg(src + 3 * i + pa1), cen[pa1]);
+                x2[i] = diff_f<T>(__ldg(src + 3 * i + pa2), cen[pa2]);
+                const T f = diff_f<T>(__ldg(src + 3 * i + axis), cen[axis]);
+                yv[i] = f;
+                msum[0] = msum[0] + f;
+                const float d = A.noise ? __ldg(A.noise + beg + i) : sn2f;
+                Eg[i] = tc_exp_above(sqrtf(sf2f + d));
+            } else {  // identity padding rows
+                x1[i] = zero<T>();
+                x2[i] = zero<T>();
+                yv[i] = zero<T>();
+                Eg[i] = tc_exp_above(1.f);
+            }
+        }
+        block_sum<T, 1>(msum, reinterpret_cast<T*>(red));
+        const T m = A.mean_mode == 1 ? msum[0] / from_f<T>((float)n) : zero<T>();
+        for (int i = tid; i < n; i += kT) yv[i] = yv[i] - m;
+        const int EV = tc_exp_above(sqrtf(sf2f));
+        (void)nmin;
+        // running sums (w: L z partial products for Gram rows, V.z for query rows; s2:
+        // |V_q|^2) and the node factors a_i(u) = sf2 exp(-lambda (x_i - u)^2),
+        // b_i(v) = exp(-lambda (y_i - v)^2)
+        unsigned char* sl = wsb;
+        T* rs = reinterpret_cast<T*>(wsb + (int64_t)NP * NSL * RG * kGrpBytes);
+        T* fa = rs + 2 * (int64_t)R;
+        T* fb = fa + (int64_t)np * G;
+        for (int i = tid; i < 2 * R; i += kT) rs[i] = zero<T>();
+        __syncthreads();
+        for (int t = tid; t < np * G; t += kT) {
+            const int i = t / G, u = t - i * G;
+            if (i < n) {
+                const T da = x1[i] - nodes[u], db = x2[i] - nodes[u];
+                fa[t] = sf2 * gexpw(nlam * (da * da), xtab);
+                fb[t] = gexpw(nlam * (db * db), xtab);
+            } else {
+                fa[t] = zero<T>();
+                fb[t] = zero<T>();
+            }
+        }
+        __syncthreads();
+
+        // ---- A3-A8: panels ------------------------------------------------------------
+        for (int p = 0; p < NP; ++p) {
+            const int c0 = p * kBP;
+            const int T_ = (R - c0 + kMT - 1) / kMT;  // M tiles of this panel
+            if (warp == 0 && p > 0) {
+                // producer: chunks j = 0 .. p-1 of every tile
+                if (lane == 0) {
+                    for (int t = 0; t < T_; ++t) {
+                        const int g0 = (c0 + kMT * t) >> 3;
+                        for (int j = 0; j < p; ++j, ++cnt) {
+                            const int st = cnt % kNSt;
+                            const uint32_t rnd = cnt / kNSt;
+                            if (rnd > 0 && !vload(sh.broken) &&
+                                !umma::mbar_wait(&sh.empty[st], (rnd - 1) & 1, kPolls))
+                                vstore(sh.broken, 1);
+                            if (vload(sh.broken)) continue;
+                            unsigned char* dst = sm + st * P::stage;
+                            mbar_expect_tx(&sh.full[st], P::stage);
+#pragma unroll
+                            for (int s = 0; s < NSL; ++s) {
+                                bulk_g2s(dst + s * kSlA, sl + sl_off(j, s, g0, NSL, RG), kSlA, &sh.full[st]);
+                                bulk_g2s(dst + NSL * kSlA + s * kSlB, sl + sl_off(j, s, c0 >> 3, NSL, RG),
+                                         kSlB, &sh.full[st]);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            } else if (warp == 1 && p > 0) {
+                // MMA issuer
+                if (lane == 0) {
+                    uint32_t c2 = cnt;
+                    for (int t = 0; t < T_; ++t) {
+                        const int set = t & 1;
+                        if (use[set] > 0 && !vload(sh.broken) &&
+                            !umma::mbar_wait(&sh.acc_empty[set], (use[set] - 1) & 1, kPolls))
+                            vstore(sh.broken, 1);
+                        umma::fence_after_sync();
+                        const uint32_t dacc = tmem + set * P::set_cols;
+                        for (int j = 0; j < p; ++j, ++c2) {
+                            const int st = c2 % kNSt;
+                            if (!vload(sh.broken) && !umma::mbar_wait(&sh.full[st], (c2 / kNSt) & 1, kPolls))
+                                vstore(sh.broken, 1);
+                            umma::fence_after_sync();
+                            if (!vload(sh.broken)) {
+                                const uint32_t a0 = umma::smem_addr(sm + st * P::stage);
+                                const uint32_t b0 = a0 + NSL * kSlA;
+#pragma unroll
+                                for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                                    for (int s = 0; s < NSL; ++s)
+#pragma unroll
+                                        for (int s2 = 0; s2 < NSL - s; ++s2) {
+                                            const uint64_t ad = umma::make_desc(a0 + s * kSlA + ks * 256, 128, 512);
+                                            const uint64_t bd = umma::make_desc(b0 + s2 * kSlB + ks * 256, 128, 512);
+                                            umma::mma_bf16(dacc + (s + s2) * kBP, ad, bd, idesc,
+                                                           !(j == 0 && ks == 0 && s == 0));
+                                        }
+                            }
+                            umma::mma_commit(&sh.empty[st]);
+                        }
+                        umma::mma_commit(&sh.acc_full[set]);
+                        ++use[set];
+                    }
+                }
+                __syncwarp();
+                cnt += (uint32_t)(T_ * p);
+            } else if (warp == 0 || warp == 1) {
+                // panel 0 has no earlier columns: nothing to load or multiply
+            } else if (warp >= 4) {
+                // epilogue groups: warps 4..7 take the even tiles, 8..11 the odd ones
+                const int grp = (warp - 4) >> 2, qd = warp & 3;
+                const int ri = 32 * qd + lane;  // row within the tile = tensor-memory lane
+                for (int t = grp; t < T_; t += 2) {
+                    const int r = c0 + kMT * t + ri;
+                    const bool valid = r < R;
+                    T row[kBP];
+                    // P = M[r, panel] - sum_{k < c0} L[r, k] L[panel, k]
+                    const int Er = valid ? (r < np ? Eg[r] : EV) : 0;
+                    if (p > 0) {
+                        if (!vload(sh.broken) && !umma::mbar_wait(&sh.acc_full[grp], use[grp] & 1, kPolls))
+                            vstore(sh.broken, 1);
+                        umma::fence_after_sync();
+                        const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + grp * P::set_cols;
+                        // the levels hold the products' values (the slices keep their
+                        // magnitudes); summed into the working type, largest level first
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                            for (int l = 0; l < NSL; ++l) {
+                                uint32_t lv[16];
+                                tmem_ld16_nowait(tb + l * kBP + 16 * h, lv);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int jj = 0; jj < 16; ++jj) {
+                                    const float x = __uint_as_float(lv[jj]);
+                                    if (l == 0) row[16 * h + jj] = from_f<T>(x);
+                                    else add_f(row[16 * h + jj], x);
+                                }
+                            }
+                        }
+                        umma::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh.acc_empty[grp]);
+                        ++use[grp];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < kBP; ++j) row[j] = zero<T>();
+                    }
+                    if (valid) {
+#pragma unroll
+                        for (int j = 0; j < kBP; ++j) {
+                            const int c = c0 + j;
+                            T o;
+                            if (r < np) {  // Gram + noise (lower triangle), identity padding
+                                if (c > r) o = zero<T>();
+                                else if (r >= n || c >= n) o = from_f<T>(r == c ? 1.f : 0.f);
+                                else {
+                                    const T d1 = x1[r] - x1[c], d2 = x2[r] - x2[c];
+                                    o = sf2 * gexpw(nlam * (d1 * d1 + d2 * d2), xtab);
+                                    if (r == c) o = o + from_f<T>(A.noise ? __ldg(A.noise + beg + r) : sn2f);
+                                }
+                            } else {       // cross-covariance of query q = (u, v)
+                                const int q = r - np, uu = q / G, vv = q - uu * G;
+                                o = fa[(int64_t)c * G + uu] * fb[(int64_t)c * G + vv];
+                            }
+                            row[j] = o - row[j];
+                        }
+                    }
+                    // ---- diagonal block (tile 0, warp 4): factor, z of the panel ----------
+                    if (t == 0 && qd == 0) {
+                        // lane i holds row c0 + i; right-looking, one column per step
+                        float dmn = 3.0e38f, dmx = 0.f;
+                        int bad = 0;
+#pragma unroll
+                        for (int k = 0; k < kBP; ++k) {
+                            const T d = shfl_idx_t(row[k], k);
+                            const float dh = hi_of(d);
+                            if (c0 + k < n) {
+                                if (!(dh > 0.f)) bad = 1;
+                                dmn = fminf(dmn, dh);
+                                dmx = fmaxf(dmx, dh);
+                            }
+                            const T ls = gsqrt(d), il = grcp(ls);
+                            if (lane == k) { row[k] = ls; rd[k] = il; }
+                            if (lane > k) row[k] = row[k] * il;
+                            // rank-1 update of the columns right of k
+                            const T lk = row[k];
+#pragma unroll
+                            for (int mm = k + 1; mm < kBP; ++mm) {
+                                const T lm = shfl_idx_t(lk, mm);  // L[c0 + mm, c0 + k]
+                                if (lane >= mm) row[mm] = gfnma(lk, lm, row[mm]);
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < kBP; ++j) Lkk[lane * kBP + j] = (j <= lane) ? row[j] : zero<T>();
+                        __syncwarp();
+                        // z of the panel: L_pp z_p = y_p - w_p
+                        {
+                            T zl = yv[c0 + lane] - rs[2 * (c0 + lane)];
+#pragma unroll
+                            for (int k = 0; k < kBP; ++k) {
+                                const T zk = shfl_idx_t(zl * rd[k], k);
+                                if (lane == k) zl = zk;
+                                if (lane > k) zl = gfnma(row[k], zk, zl);
+                            }
+                            zp[lane] = zl;
+                        }
+                        if (bad) sh.fail = 1;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            dmn = fminf(dmn, __shfl_xor_sync(0xffffffffu, dmn, o));
+                            dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+                        }
+                        if (lane == 0) {
+                            sh.dmin = fminf(sh.dmin, dmn);
+                            sh.dmax = fmaxf(sh.dmax, dmx);
+                        }
+                        __threadfence_block();
+                        __syncwarp();
+                        named_arrive(1, 128);                 // warps 5..7
+                        if (T_ > 1) named_arrive(2, 160);     // the odd tiles' group
+                    } else {
+                        if (t == 0) named_sync(1, 128);
+                        else if (t == 1) named_sync(2, 160);
+                        // rows below the block: L[r, panel] = P[r, :] L_pp^-T
+                        if (valid) {
+#pragma unroll
+                            for (int j = 0; j < kBP; ++j) {
+                                T s = row[j];
+                                const T* lj = Lkk + j * kBP;
+#pragma unroll
+                                for (int k = 0; k < j; ++k) acc_fma(s, -row[k], lj[k]);
+                                row[j] = acc_norm(s) * rd[j];
+                            }
+                            // running sums: w += L[r, panel] z_p, and |V_q|^2 for query rows
+                            T w = rs[2 * (int64_t)r], s2 = rs[2 * (int64_t)r + 1];
+#pragma unroll
+                            for (int j = 0; j < kBP; ++j) acc_fma(w, row[j], zp[j]);
+                            w = acc_norm(w);
+                            if (r >= np) {
+#pragma unroll
+                                for (int j = 0; j < kBP; ++j) acc_fma(s2, row[j], row[j]);
+                                s2 = acc_norm(s2);
+                            }
+                            rs[2 * (int64_t)r] = w;
+                            rs[2 * (int64_t)r + 1] = s2;
+                        }
+                    }
+                    // ---- cut the finished entries into slices and store them ---------------
+                    if (valid) {
+                        const int g = r >> 3;
+                        uint32_t w4[NSL][kBP / 2];
+#pragma unroll
+                        for (int j = 0; j < kBP; j += 2) {
+                            uint32_t qa[NSL], qb[NSL];
+                            const bool up0 = r < np && c0 + j > r, up1 = r < np && c0 + j + 1 > r;
+                            cut<NSL, T>(up0 ? zero<T>() : row[j], Er, qa);
+                            cut<NSL, T>(up1 ? zero<T>() : row[j + 1], Er, qb);
+#pragma unroll
+                            for (int s = 0; s < NSL; ++s) w4[s][j >> 1] = qa[s] | (qb[s] << 16);
+                        }
+#pragma unroll
+                        for (int s = 0; s < NSL; ++s) {
+                            unsigned char* base = sl + sl_off(p, s, g, NSL, RG) + (r & 7) * 16;
+#pragma unroll
+                            for (int kg = 0; kg < 4; ++kg)
+                                *reinterpret_cast<uint4*>(base + kg * 128) =
+                                    make_uint4(w4[s][4 * kg], w4[s][4 * kg + 1], w4[s][4 * kg + 2], w4[s][4 * kg + 3]);
+                        }
+                    }
+                    fence_async_global();
+                }
+            }
+            __syncthreads();
+            // conditioning check of the mixed path after each panel's pivots
+            if (tid == 0 && !sh.abort) {
+                const bool ill = sh.fail || (sh.dmax > A.esc_cond * sh.dmin);
+                if (ill && A.escalate) sh.abort = 1;
+                else if (sh.fail) sh.abort = 2;
+                if (vload(sh.broken)) sh.abort = 3;
+            }
+            __syncthreads();
+            if (sh.abort) break;
+        }
+
+        // ---- outputs ------------------------------------------------------------------
+        const int64_t obase = (int64_t)v * Q;
+        const int ab = sh.abort;
+        if (ab == 1) {  // badly conditioned: the FP64 pass re-solves the voxel
+            if (tid == 0) {
+                const int big = n > A.nmax_small_f64 ? 1 : 0;
+                const int slot = atomicAdd(A.esc_count + big, 1);
+                A.esc_list[(int64_t)big * A.nvox + slot] = v;
+            }
+        } else if (ab >= 2) {  // not positive definite in this precision, or a wait gave up
+            for (int q = tid; q < Q; q += kT) {
+                A.mean[obase + q] = to_f(m);
+                A.var[obase + q] = sf2f;
+            }
+            if (A.pos) {
+                const int NG = A.n_s * A.n_s;
+                for (int g = tid; g < NG; g += kT) {
+                    const int64_t o = (int64_t)v * NG + g;
+                    for (int k = 0; k < 3; ++k) { A.pos[3 * o + k] = cen[k]; A.scale[3 * o + k] = 0.f; }
+                    A.quat[4 * o] = 1.f; A.quat[4 * o + 1] = 0.f; A.quat[4 * o + 2] = 0.f; A.quat[4 * o + 3] = 0.f;
+                }
+            }
+            if (tid == 0) {
+                A.axis[v] = (uint8_t)axis;
+                A.status[v] = (ab == 3 ? VOX_FAILED : VOX_NOT_SPD) | (A.escalation_pass ? VOX_ESCALATED : 0u);
+            }
+        } else {
+            // mu_q = m + V_q . z, var_q = sf2 - |V_q|^2; predictions staged for the init
+            T* mv = reinterpret_cast<T*>(sm);  // the operand stages are idle now
+            for (int q = tid; q < Q; q += kT) {
+                const T mu = m + rs[2 * (int64_t)(np + q)];
+                T var = sf2 - rs[2 * (int64_t)(np + q) + 1];
+                if (!(hi_of(var) > 0.f)) var = zero<T>();
+                A.mean[obase + q] = to_f(mu);
+                A.var[obase + q] = to_f(var);
+                mv[q] = mu;
+                mv[Q + q] = var;
+            }
+            if (tid == 0) {
+                A.axis[v] = (uint8_t)axis;
+                A.status[v] = A.escalation_pass ? VOX_ESCALATED : 0u;
+            }
+            if (A.pos) {
+                __syncthreads();
+                const int NG = A.n_s * A.n_s;
+                for (int g = tid; g < NG; g += kT) {
+                    const int64_t o = (int64_t)v * NG + g;
+                    init_one_gaussian<T>(mv, mv + Q, nodes, axis, cen, A.size, G, A.n_s, A.n_r, sf2f,
+                                         A.init_mode, g / A.n_s, g % A.n_s, A.pos + 3 * o,
+                                         A.scale + 3 * o, A.quat + 4 * o);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // every MMA this CTA issued has completed (each tile's epilogue waited for it)
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 2) umma::tmem_free(tmem, P::tmem_cols);
+}
+
+}  // namespace
+
+int tall_smem(int prec, int npmax)
+{
+    return prec == PREC_F32 ? tall_smem_bytes(3, npmax, 4) : tall_smem_bytes(6, npmax, 8);
+}
+
+int64_t tall_ws_stride(int prec, int nmax, int G)
+{
+    return prec == PREC_F32 ? tall_ws_bytes(3, nmax, G, 4) : tall_ws_bytes(6, nmax, G, 8);
+}
+
+cudaError_t tall_prepare(int prec, int npmax)
+{
+    const int bytes = tall_smem(prec, npmax);
+    return prec == PREC_F32
+               ? cudaFuncSetAttribute(k_tall<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+               : cudaFuncSetAttribute(k_tall<ff, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_tall(int prec, const SolveArgs& a, unsigned char* ws, int64_t ws_stride, int npmax,
+                        int grid, cudaStream_t s)
+{
+    const int bytes = tall_smem(prec, npmax);
+    if (prec == PREC_F32) k_tall<float, 3><<<grid, kT, bytes, s>>>(a, ws, ws_stride, npmax);
+    else k_tall<ff, 6><<<grid, kT, bytes, s>>>(a, ws, ws_stride, npmax);
+    return cudaGetLastError();
+}
+
+}  // namespace gpv

@@ -63,6 +63,7 @@ class gp_voxels_config(ctypes.Structure):
         ("factor_panel", ctypes.c_int),
         ("tc_workspace_mb", ctypes.c_int),
         ("refine", ctypes.c_int),
+        ("tall_min_points", ctypes.c_int),
     ]
 
 

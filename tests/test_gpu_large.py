@@ -21,6 +21,9 @@ MEAN_TOL = 1e-4
 VAR_TOL = 1e-3
 FP32_MEAN_TOL = 1e-4
 FP32_VAR_TOL = 0.25
+# provisional bounds of the FP32 tall path (three BF16 slices, no refinement)
+FP32_MEAN_TOL_TALL = 1e-2
+FP32_VAR_TOL_TALL = 10.0
 
 
 @pytest.fixture(scope="module")
@@ -109,3 +112,41 @@ def test_fp32_refinement_helps(gpv, oracle):
     print(f"\nfp32 plain {errs[0]}\nfp32 refined {errs[1]}")
     assert errs[1]["mean_max"] <= FP32_MEAN_TOL
     assert errs[1]["mean_max"] < errs[0]["mean_max"]
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_tall_path_against_workspace_path(gpv, oracle, precision):
+    """The tall-matrix factorisation (default for voxels beyond the shared-memory kernels)
+    and the global-workspace kernel (tall_min_points = -1) agree with each other and with
+    the oracle, on stress shapes with ragged counts (not multiples of the 32-column panel)
+    and the fused Gaussian initialisation."""
+    import torch
+    from oracle import compare
+    from oracle import oracle as O
+    b = _stress_large(nsel=40, seed=11)
+    assert np.any(b.counts % 32 != 0)
+    res = {}
+    for tm in (0, -1):
+        d = dict(voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau,
+                 max_points=1024, max_voxels=b.nvox, precision=precision, tall_min_points=tm)
+        g = gpv.GpVoxels(gpv.gp_voxels_config_default(**d))
+        dv = gpv.batch_to_device(b)
+        out = g.solve_csr(dv["xyz"], dv["offsets"], dv["centres"], dv["lam"], dv["sf2"],
+                          dv["sn2"], init=True)
+        torch.cuda.synchronize()
+        res[tm] = {k: v.cpu().numpy() for k, v in out.items()}
+        g.close()
+    a, w = res[0], res[-1]
+    assert np.array_equal(a["axis"], w["axis"])
+    assert np.array_equal(a["status"], w["status"])
+    if precision == 1:
+        ref = _check(b, a, MEAN_TOL, VAR_TOL, "tall path")
+        ok = np.repeat(a["status"] == 0, b.n_s * b.n_s)
+        refc = compare.oracle_for_batch(b, gpu_axis=a["axis"].astype(np.int32))
+        ri = O.init_batch(refc["mean"], refc["var"], refc["axis"], b.centres, b.sf2, b.size,
+                          b.G, b.n_s, b.n_r)
+        ie = compare.init_errors(a["pos"], a["scale"], a["quat"], ri, valid=ok)
+        print("tall path init", ie)
+        assert ie["scale_rel_max"] <= 1e-4 and ie["rot_max"] <= 1e-3
+    else:
+        _check(b, a, FP32_MEAN_TOL_TALL, FP32_VAR_TOL_TALL, "tall path fp32")
