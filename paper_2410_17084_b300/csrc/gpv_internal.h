@@ -216,7 +216,7 @@ cudaError_t solve_occupancy(int prec, bool tri_in_smem, int nthr, int smem, int*
                             bool tcv = false);
 cudaError_t launch_var_tc(const SolveArgs& a, int sms, cudaStream_t s);
 // Large voxels: blocked Cholesky of the tall matrix [K + D; K*^T] on the tensor cores
-// (gpv_tall.cu).  prec PREC_FF (six BF16 slices) or PREC_F32 (three); npmax = largest n
+// (gpv_tall.cu).  prec PREC_FF (six BF16 slices) or PREC_F32 (four); npmax = largest n
 // of the launch rounded up to 32; ws holds one slice store of tall_ws_stride() bytes per
 // CTA; grid = CTAs (one per SM).
 int tall_smem(int prec, int npmax);

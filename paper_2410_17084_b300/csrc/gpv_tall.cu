@@ -32,8 +32,9 @@
 // over the row norms, level 0 stays below 2^14 grid units and level 1 below 2^20 for any
 // K; the levels of remainder slices (products of up to 2^14 units, signs close to
 // random) grow like sqrt(K) 2^14 / 3 (2^17.4 at K = 1024, against 2^24 for exactness).
-// The mixed path uses NSL = 6 (48 bits, 21 products per element); the FP32 path NSL = 3
-// (24 bits, 6 products).  Pairs with s + t >= NSL are dropped (below 2^-8 NSL of the row
+// The mixed path uses NSL = 6 (48 bits, 21 products per element); the FP32 path NSL = 4
+// (32 bits, 10 products: the fixed-point grid of a row then resolves entries well below
+// the row's norm to about FP32's own precision).  Pairs with s + t >= NSL are dropped (below 2^-8 NSL of the row
 // scale).  The diagonal-block factor, the solves against it and the running sums are in
 // the working type (float-float or FP32) on the CUDA cores.
 //
@@ -73,13 +74,14 @@ template <int NSL> struct Plan {
     static constexpr int tmem_cols = 2 * set_cols <= 256 ? 256 : 512;
 };
 
-// dynamic shared memory: [stages][x1, x2, y: np each][Lkk 32x32][rd 32][zp 32][Eg: np]
+constexpr int kLs = kBP + 1;  // row stride of the diagonal-block buffers (bank spread)
+
+// dynamic shared memory: [stages][x1, x2: np each][Lkk, D: 32 x 33 each][rd, zp: 32]
 __host__ __device__ inline int tall_smem_bytes(int nsl, int npmax, int tsize)
 {
     int o = kNSt * nsl * (kSlA + kSlB);
-    o += 3 * npmax * tsize;
-    o += (kBP * kBP + 2 * kBP) * tsize;
-    o += 4 * npmax;
+    o += 2 * npmax * tsize;
+    o += (2 * kBP * kLs + 2 * kBP) * tsize;
     return (o + 15) & ~15;
 }
 
@@ -125,11 +127,6 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ float shfl_idx_t(float x, int src) { return __shfl_sync(0xffffffffu, x, src); }
-__device__ __forceinline__ ff shfl_idx_t(ff x, int src)
-{
-    return ff_make(__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src));
-}
 // x += y (y a float) with an unnormalised float-float accumulator
 __device__ __forceinline__ void add_f(float& x, float y) { x = __fadd_rn(x, y); }
 __device__ __forceinline__ void add_f(ff& x, float y)
@@ -183,7 +180,14 @@ struct Sh {  // static shared state
 
 }  // namespace
 
-// Workspace of one CTA: slice store, per-row running sums, node factors.
+// Entries of K + D kept per panel: rows c0 .. np-1 of panel p, 32 values each.
+__host__ __device__ inline int64_t tall_gram_off(int p, int np)
+{
+    return (int64_t)kBP * ((int64_t)p * np - (int64_t)kBP * p * (p - 1) / 2);
+}
+__host__ __device__ inline int64_t tall_gram_elems(int np) { return tall_gram_off(np / kBP, np); }
+
+// Workspace of one CTA: slice store, per-row running sums, node factors, K + D.
 __host__ __device__ inline int tall_np(int n) { return (n + kBP - 1) / kBP * kBP; }
 __host__ __device__ inline int tall_rg(int np, int Q) { return (np + Q + kMT + 7) / 8; }
 __host__ __device__ inline int64_t tall_ws_bytes(int nsl, int nmax, int G, int tsize)
@@ -192,7 +196,9 @@ __host__ __device__ inline int64_t tall_ws_bytes(int nsl, int nmax, int G, int t
     const int64_t sl = (int64_t)(np / kBP) * nsl * tall_rg(np, Q) * kGrpBytes;
     const int64_t rs = (int64_t)2 * (np + Q) * tsize;   // running sums w, s2 per row
     const int64_t ab = (int64_t)2 * np * G * tsize;     // node factors a(u), b(v)
-    return (sl + rs + ab + 255) & ~(int64_t)255;
+    const int64_t gr = tall_gram_elems(np) * tsize;     // K + D, panel by panel
+    const int64_t yE = (int64_t)np * (tsize + 4);       // targets f - m, row exponents
+    return (sl + rs + ab + gr + yE + 255) & ~(int64_t)255;
 }
 
 namespace {
@@ -213,11 +219,10 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
 
     T* x1 = reinterpret_cast<T*>(sm + kNSt * P::stage);
     T* x2 = x1 + npmax;
-    T* yv = x2 + npmax;
-    T* Lkk = yv + npmax;       // 32 x 32, row-major
-    T* rd = Lkk + kBP * kBP;   // 1 / L_jj
+    T* Lkk = x2 + npmax;       // L of the diagonal block, 32 x 33, row-major
+    T* Dm = Lkk + kBP * kLs;   // its inverse (lower triangle, zeros above)
+    T* rd = Dm + kBP * kLs;    // 1 / L_jj
     T* zp = rd + kBP;          // z of the panel
-    int* Eg = reinterpret_cast<int*>(zp + kBP);
 
     if (threadIdx.x < G)
         nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
@@ -294,6 +299,17 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
         const int pa2 = axis == 0 ? 2 : (axis == 1 ? 0 : 1);
         const float cen[3] = {cx, cy, cz};
         const float lamf = A.lam[v], sf2f = A.sf2[v], sn2f = A.sn2[v];
+        // global part of the workspace: slices, running sums (w: the partial products
+        // L z of Gram rows and V . z of query rows; s2: |V_q|^2), the node factors
+        // a_i(u) = sf2 exp(-lambda (x_i - u)^2), b_i(v) = exp(-lambda (y_i - v)^2), K + D by
+        // panels, the targets f - m and the row exponents
+        unsigned char* sl = wsb;
+        T* rs = reinterpret_cast<T*>(wsb + (int64_t)NP * NSL * RG * kGrpBytes);
+        T* fa = rs + 2 * (int64_t)R;
+        T* fb = fa + (int64_t)np * G;
+        T* gram = fb + (int64_t)np * G;
+        T* yv = gram + tall_gram_elems(np);
+        int* Eg = reinterpret_cast<int*>(yv + np);
         const T nlam = from_f<T>(-lamf), sf2 = from_f<T>(sf2f);
         T msum[1] = {zero<T>()};
         float nmin = 3.0e38f;
@@ -318,13 +334,6 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
         for (int i = tid; i < n; i += kT) yv[i] = yv[i] - m;
         const int EV = tc_exp_above(sqrtf(sf2f));
         (void)nmin;
-        // running sums (w: L z partial products for Gram rows, V.z for query rows; s2:
-        // |V_q|^2) and the node factors a_i(u) = sf2 exp(-lambda (x_i - u)^2),
-        // b_i(v) = exp(-lambda (y_i - v)^2)
-        unsigned char* sl = wsb;
-        T* rs = reinterpret_cast<T*>(wsb + (int64_t)NP * NSL * RG * kGrpBytes);
-        T* fa = rs + 2 * (int64_t)R;
-        T* fb = fa + (int64_t)np * G;
         for (int i = tid; i < 2 * R; i += kT) rs[i] = zero<T>();
         __syncthreads();
         for (int t = tid; t < np * G; t += kT) {
@@ -336,6 +345,24 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
             } else {
                 fa[t] = zero<T>();
                 fb[t] = zero<T>();
+            }
+        }
+        // A3: K + D (lower triangle; identity on the padding), stored panel by panel so
+        // that each row's 32 entries of a panel are contiguous
+        for (int pp = 0; pp < NP; ++pp) {
+            const int cc0 = pp * kBP;
+            T* gp = gram + tall_gram_off(pp, np);
+            for (int e = tid; e < (np - cc0) * kBP; e += kT) {
+                const int r = cc0 + (e >> 5), c = cc0 + (e & 31);
+                T o;
+                if (c > r) o = zero<T>();
+                else if (r >= n || c >= n) o = from_f<T>(r == c ? 1.f : 0.f);
+                else {
+                    const T d1 = x1[r] - x1[c], d2 = x2[r] - x2[c];
+                    o = sf2 * gexpw(nlam * (d1 * d1 + d2 * d2), xtab);
+                    if (r == c) o = o + from_f<T>(A.noise ? __ldg(A.noise + beg + r) : sn2f);
+                }
+                gp[e] = o;
             }
         }
         __syncthreads();
@@ -449,34 +476,29 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
 #pragma unroll
                         for (int j = 0; j < kBP; ++j) row[j] = zero<T>();
                     }
-                    if (valid) {
+                    if (valid) {  // P = M[r, panel] - (the products of the earlier columns)
+                        if (r < np) {
+                            const T* gp = gram + tall_gram_off(p, np) + (int64_t)(r - c0) * kBP;
 #pragma unroll
-                        for (int j = 0; j < kBP; ++j) {
-                            const int c = c0 + j;
-                            T o;
-                            if (r < np) {  // Gram + noise (lower triangle), identity padding
-                                if (c > r) o = zero<T>();
-                                else if (r >= n || c >= n) o = from_f<T>(r == c ? 1.f : 0.f);
-                                else {
-                                    const T d1 = x1[r] - x1[c], d2 = x2[r] - x2[c];
-                                    o = sf2 * gexpw(nlam * (d1 * d1 + d2 * d2), xtab);
-                                    if (r == c) o = o + from_f<T>(A.noise ? __ldg(A.noise + beg + r) : sn2f);
-                                }
-                            } else {       // cross-covariance of query q = (u, v)
-                                const int q = r - np, uu = q / G, vv = q - uu * G;
-                                o = fa[(int64_t)c * G + uu] * fb[(int64_t)c * G + vv];
-                            }
-                            row[j] = o - row[j];
+                            for (int j = 0; j < kBP; ++j) row[j] = gp[j] - row[j];
+                        } else {  // cross-covariance of query q = (u, v)
+                            const int q = r - np, uu = q / G, vv = q - uu * G;
+#pragma unroll
+                            for (int j = 0; j < kBP; ++j)
+                                row[j] = fa[(int64_t)(c0 + j) * G + uu] * fb[(int64_t)(c0 + j) * G + vv] - row[j];
                         }
                     }
-                    // ---- diagonal block (tile 0, warp 4): factor, z of the panel ----------
-                    if (t == 0 && qd == 0) {
-                        // lane i holds row c0 + i; right-looking, one column per step
+                    const bool diag = t == 0 && qd == 0;  // warp 4: the rows of the diagonal block
+                    if (diag) {
+                        // ---- factor the diagonal block, invert it, z of the panel ------------
+#pragma unroll
+                        for (int j = 0; j < kBP; ++j) Lkk[lane * kLs + j] = row[j];
+                        __syncwarp();
                         float dmn = 3.0e38f, dmx = 0.f;
                         int bad = 0;
-#pragma unroll
-                        for (int k = 0; k < kBP; ++k) {
-                            const T d = shfl_idx_t(row[k], k);
+                        for (int k = 0; k < kBP; ++k) {  // right-looking, one column per step
+                            __syncwarp();
+                            const T d = Lkk[k * kLs + k];
                             const float dh = hi_of(d);
                             if (c0 + k < n) {
                                 if (!(dh > 0.f)) bad = 1;
@@ -484,29 +506,35 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                                 dmx = fmaxf(dmx, dh);
                             }
                             const T ls = gsqrt(d), il = grcp(ls);
-                            if (lane == k) { row[k] = ls; rd[k] = il; }
-                            if (lane > k) row[k] = row[k] * il;
-                            // rank-1 update of the columns right of k
-                            const T lk = row[k];
-#pragma unroll
-                            for (int mm = k + 1; mm < kBP; ++mm) {
-                                const T lm = shfl_idx_t(lk, mm);  // L[c0 + mm, c0 + k]
-                                if (lane >= mm) row[mm] = gfnma(lk, lm, row[mm]);
+                            __syncwarp();
+                            if (lane == k) { Lkk[k * kLs + k] = ls; rd[k] = il; }
+                            if (lane > k) Lkk[lane * kLs + k] = Lkk[lane * kLs + k] * il;
+                            __syncwarp();
+                            if (lane > k) {
+                                const T lik = Lkk[lane * kLs + k];
+                                for (int mm = k + 1; mm <= lane; ++mm)
+                                    Lkk[lane * kLs + mm] = gfnma(lik, Lkk[mm * kLs + k], Lkk[lane * kLs + mm]);
                             }
                         }
-#pragma unroll
-                        for (int j = 0; j < kBP; ++j) Lkk[lane * kBP + j] = (j <= lane) ? row[j] : zero<T>();
                         __syncwarp();
-                        // z of the panel: L_pp z_p = y_p - w_p
+                        // D = L_pp^-1, lane j forms column j
+                        for (int i = 0; i < kBP; ++i) Dm[i * kLs + lane] = zero<T>();
+                        __syncwarp();
+                        Dm[lane * kLs + lane] = rd[lane];
+                        for (int i = lane + 1; i < kBP; ++i) {
+                            T acc = zero<T>();
+                            for (int k = lane; k < i; ++k) acc_fma(acc, Lkk[i * kLs + k], Dm[k * kLs + lane]);
+                            Dm[i * kLs + lane] = -(acc_norm(acc) * rd[i]);
+                        }
+                        __syncwarp();
+                        // z_p = D (y_p - w_p)
                         {
-                            T zl = yv[c0 + lane] - rs[2 * (c0 + lane)];
-#pragma unroll
-                            for (int k = 0; k < kBP; ++k) {
-                                const T zk = shfl_idx_t(zl * rd[k], k);
-                                if (lane == k) zl = zk;
-                                if (lane > k) zl = gfnma(row[k], zk, zl);
-                            }
-                            zp[lane] = zl;
+                            zp[lane] = yv[c0 + lane] - rs[2 * (c0 + lane)];
+                            __syncwarp();
+                            T zl = zero<T>();
+                            for (int k = 0; k <= lane; ++k) acc_fma(zl, Dm[lane * kLs + k], zp[k]);
+                            __syncwarp();
+                            zp[lane] = acc_norm(zl);
                         }
                         if (bad) sh.fail = 1;
                         for (int o = 16; o > 0; o >>= 1) {
@@ -524,50 +552,54 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                     } else {
                         if (t == 0) named_sync(1, 128);
                         else if (t == 1) named_sync(2, 160);
-                        // rows below the block: L[r, panel] = P[r, :] L_pp^-T
-                        if (valid) {
-#pragma unroll
-                            for (int j = 0; j < kBP; ++j) {
-                                T s = row[j];
-                                const T* lj = Lkk + j * kBP;
-#pragma unroll
-                                for (int k = 0; k < j; ++k) acc_fma(s, -row[k], lj[k]);
-                                row[j] = acc_norm(s) * rd[j];
-                            }
-                            // running sums: w += L[r, panel] z_p, and |V_q|^2 for query rows
-                            T w = rs[2 * (int64_t)r], s2 = rs[2 * (int64_t)r + 1];
-#pragma unroll
-                            for (int j = 0; j < kBP; ++j) acc_fma(w, row[j], zp[j]);
-                            w = acc_norm(w);
-                            if (r >= np) {
-#pragma unroll
-                                for (int j = 0; j < kBP; ++j) acc_fma(s2, row[j], row[j]);
-                                s2 = acc_norm(s2);
-                            }
-                            rs[2 * (int64_t)r] = w;
-                            rs[2 * (int64_t)r + 1] = s2;
-                        }
                     }
-                    // ---- cut the finished entries into slices and store them ---------------
+                    // ---- L[r, panel] = P[r, :] D^T (the diagonal rows take L_pp itself), the
+                    // running sums, the slices: two columns per step ------------------------
                     if (valid) {
+                        T w = rs[2 * (int64_t)r], s2 = rs[2 * (int64_t)r + 1];
+                        const bool qrow = r >= np;
                         const int g = r >> 3;
-                        uint32_t w4[NSL][kBP / 2];
+                        unsigned char* base = sl + sl_off(p, 0, g, NSL, RG) + (r & 7) * 16;
+                        const int64_t sstride = (int64_t)RG * kGrpBytes;  // next slice
+                        // columns in four blocks of 8: D is lower triangular, so the dot
+                        // products of block jb stop at column 8 jb + 7
 #pragma unroll
-                        for (int j = 0; j < kBP; j += 2) {
-                            uint32_t qa[NSL], qb[NSL];
-                            const bool up0 = r < np && c0 + j > r, up1 = r < np && c0 + j + 1 > r;
-                            cut<NSL, T>(up0 ? zero<T>() : row[j], Er, qa);
-                            cut<NSL, T>(up1 ? zero<T>() : row[j + 1], Er, qb);
+                        for (int jb = 0; jb < kBP / 8; ++jb) {
+                            for (int j = 8 * jb; j < 8 * jb + 8; j += 2) {
+                                T l0, l1;
+                                if (diag) {
+                                    l0 = j <= lane ? Lkk[lane * kLs + j] : zero<T>();
+                                    l1 = j + 1 <= lane ? Lkk[lane * kLs + j + 1] : zero<T>();
+                                } else {
+                                    T a0 = zero<T>(), a1 = zero<T>();
+                                    const T* d0 = Dm + j * kLs;
+                                    const T* d1 = d0 + kLs;
 #pragma unroll
-                            for (int s = 0; s < NSL; ++s) w4[s][j >> 1] = qa[s] | (qb[s] << 16);
+                                    for (int k = 0; k < 8 * jb + 8; ++k) {
+                                        acc_fma(a0, row[k], d0[k]);
+                                        acc_fma(a1, row[k], d1[k]);
+                                    }
+                                    l0 = acc_norm(a0);
+                                    l1 = acc_norm(a1);
+                                    acc_fma(w, l0, zp[j]);
+                                    acc_fma(w, l1, zp[j + 1]);
+                                    if (qrow) {
+                                        acc_fma(s2, l0, l0);
+                                        acc_fma(s2, l1, l1);
+                                    }
+                                }
+                                uint32_t qa[NSL], qb[NSL];
+                                cut<NSL, T>(l0, Er, qa);
+                                cut<NSL, T>(l1, Er, qb);
+                                unsigned char* o = base + (j >> 3) * 128 + (j & 7) * 2;
+#pragma unroll
+                                for (int ss = 0; ss < NSL; ++ss)
+                                    *reinterpret_cast<uint32_t*>(o + ss * sstride) = qa[ss] | (qb[ss] << 16);
+                            }
                         }
-#pragma unroll
-                        for (int s = 0; s < NSL; ++s) {
-                            unsigned char* base = sl + sl_off(p, s, g, NSL, RG) + (r & 7) * 16;
-#pragma unroll
-                            for (int kg = 0; kg < 4; ++kg)
-                                *reinterpret_cast<uint4*>(base + kg * 128) =
-                                    make_uint4(w4[s][4 * kg], w4[s][4 * kg + 1], w4[s][4 * kg + 2], w4[s][4 * kg + 3]);
+                        if (!diag) {
+                            rs[2 * (int64_t)r] = acc_norm(w);
+                            rs[2 * (int64_t)r + 1] = acc_norm(s2);
                         }
                     }
                     fence_async_global();
@@ -650,19 +682,19 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
 
 int tall_smem(int prec, int npmax)
 {
-    return prec == PREC_F32 ? tall_smem_bytes(3, npmax, 4) : tall_smem_bytes(6, npmax, 8);
+    return prec == PREC_F32 ? tall_smem_bytes(4, npmax, 4) : tall_smem_bytes(6, npmax, 8);
 }
 
 int64_t tall_ws_stride(int prec, int nmax, int G)
 {
-    return prec == PREC_F32 ? tall_ws_bytes(3, nmax, G, 4) : tall_ws_bytes(6, nmax, G, 8);
+    return prec == PREC_F32 ? tall_ws_bytes(4, nmax, G, 4) : tall_ws_bytes(6, nmax, G, 8);
 }
 
 cudaError_t tall_prepare(int prec, int npmax)
 {
     const int bytes = tall_smem(prec, npmax);
     return prec == PREC_F32
-               ? cudaFuncSetAttribute(k_tall<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+               ? cudaFuncSetAttribute(k_tall<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
                : cudaFuncSetAttribute(k_tall<ff, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -670,7 +702,7 @@ cudaError_t launch_tall(int prec, const SolveArgs& a, unsigned char* ws, int64_t
                         int grid, cudaStream_t s)
 {
     const int bytes = tall_smem(prec, npmax);
-    if (prec == PREC_F32) k_tall<float, 3><<<grid, kT, bytes, s>>>(a, ws, ws_stride, npmax);
+    if (prec == PREC_F32) k_tall<float, 4><<<grid, kT, bytes, s>>>(a, ws, ws_stride, npmax);
     else k_tall<ff, 6><<<grid, kT, bytes, s>>>(a, ws, ws_stride, npmax);
     return cudaGetLastError();
 }
