@@ -1,13 +1,16 @@
 """Benchmark of the B300 Voxel-GPR path (GS-LIVM Sec. 3.1-3.2).
 
-One step = one batched Voxel-GPR solve + fused Gaussian initialisation over the whole
-workload: 50,000 voxels with lognormal point counts (median 64, clipped to 16..256) on
-quadric surfaces, per-voxel lengthscale U[0.1, 0.4] and noise sd U[0.01, 0.05], a 16 x 16
-query grid (n_s = n_r = 4), mixed precision (float-float with FP64 escalation).
+One step = one batched Voxel-GPR solve + fused Gaussian initialisation over the largest
+workload: 1,000,000 voxels with power-law point counts (density n^-1.5 on [4, 1024]) on
+quadric surfaces, per-voxel lengthscale U[0.1, 0.4] and noise sd U[0.01, 0.05], a 9 x 9
+query grid (n_s = n_r = 3), mixed precision (float-float and exact BF16 slice products on
+the tensor cores, FP64 escalation), replayed as one CUDA graph per step.
 
-Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the
-same workload instead (bounded sample per step).  Multi-GPU (torchrun): every rank
-solves its own independent batch (weak scaling, no data-path collective).
+Prints ONE JSON line (rank 0).  Every measured leg carries its error against the FP64
+oracle on a fixed sample of voxels solved outside the timed region.  ``--impl reference``
+times the FP64 CPU oracle on the same workload instead (bounded sample per step).
+Multi-GPU (torchrun): every rank solves its own independent batch (weak scaling, no
+data-path collective).
 """
 from __future__ import annotations
 
@@ -27,21 +30,49 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("voxel GP solves/sec + predicted pts/sec (mixed vs plain FP32, same err); "
           "p50/p99 scan ms")
-WORKLOAD = ("quadric50k: 50,000 voxels of 0.5 m, lognormal counts (median 64) clipped to "
-            "[16,256], quadric surfaces (curvature U[-2,2]) with noise sd U[0.01,0.05] m, SE "
-            "kernel lengthscale U[0.1,0.4], 16x16 query grid (n_s=n_r=4), value axis drawn "
-            "per voxel; GPR + fused Gaussian init")
+WORKLOAD = ("stress1m: 1,000,000 voxels of 0.5 m, point counts power-law (density n^-1.5) on "
+            "[4,1024], quadric surfaces (curvature U[-2,2]) with noise sd U[0.01,0.05] m, SE "
+            "kernel lengthscale U[0.1,0.4], 9x9 query grid (n_s=n_r=3), value axis drawn per "
+            "voxel; GPR + fused Gaussian init (9 Gaussians per voxel); one CUDA-graph replay "
+            "per step")
+ERR_SAMPLE = 2000          # voxels per workload compared with the oracle
+FF_OPS_PER_FMA = 12        # FP32 instructions per float-float multiply-add (accumulate form)
+SLICE_PAIRS = 21           # BF16 slice products per float-float product (six slices, s+t <= 5)
 
 
-def algorithmic_flops(counts: np.ndarray, G: int) -> float:
-    """Per voxel n^3/3 (Cholesky) + n^2 G^2 (triangular solve behind diag Sigma*) +
-    4 n G^2 (mean and variance norms) + 4 n^2 (alpha solves); the explicit inverse and
-    the full Sigma* that the method avoids are not counted."""
+# ---- algorithmic work -----------------------------------------------------------------
+def algorithmic_flops(counts: np.ndarray, G: int) -> np.ndarray:
+    """Per voxel: n^3/3 (Cholesky) + n^2 G^2 (the triangular solve behind diag Sigma*) +
+    4 n G^2 (mean and variance norms) + 4 n^2 (alpha solves); the explicit inverse and the
+    full Sigma* that the method avoids are not counted."""
     n = counts.astype(np.float64)
     g2 = float(G * G)
-    return float(np.sum(n ** 3 / 3.0 + n * n * g2 + 4.0 * n * g2 + 4.0 * n * n))
+    return n ** 3 / 3.0 + n * n * g2 + 4.0 * n * g2 + 4.0 * n * n
 
 
+def split_flops(counts: np.ndarray, G: int, plan: dict) -> dict:
+    """Algorithmic FLOPs by the unit that executes them in the mixed path.
+    Tall-matrix voxels (n > tall_min): the panel updates of L and V (all but the work
+    inside each 32-column panel) run as exact BF16 slice products on the tensor cores; the
+    in-panel work (about 32 flops per row and column: the block solve, the running sums)
+    on the CUDA cores in float-float.  Shared-memory voxels: the variance contraction
+    n^2 G^2 on the tensor cores where the tensor-core variance takes them
+    (n <= tc_nmax), everything else in float-float on the CUDA cores."""
+    n = counts.astype(np.float64)
+    fl = algorithmic_flops(counts, G)
+    Q = float(G * G)
+    tmin = plan["tall_min"] if plan["tall_min"] > 0 else 1 << 30
+    tall = counts > tmin
+    npad = np.ceil(n / 32.0) * 32.0
+    in_panel = np.minimum(32.0 * (npad + Q) * npad, fl)
+    tc_small = (~tall) & (counts <= plan["tc_nmax"])
+    f_tc = np.where(tall, fl - in_panel, np.where(tc_small, n * n * Q, 0.0))
+    return {"total": float(fl.sum()), "tc": float(f_tc.sum()), "ff": float((fl - f_tc).sum()),
+            "tall_total": float(fl[tall].sum()), "tall_tc": float(f_tc[tall].sum()),
+            "tall_ff": float(in_panel[tall].sum()), "tall_voxels": int(tall.sum())}
+
+
+# ---- clocks -----------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
 
@@ -56,11 +87,11 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -97,66 +128,111 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def fp32_alu_peak_tflops(sm_mhz: float) -> float:
-    """148 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
-    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs"), "bf16_tflops": d.get("bf16_tflops"),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "source": "fallback"}
 
 
-# FP32 instructions per float-float multiply-add in the dominant loop (the contraction
-# behind diag Sigma*): TwoProduct (2), two cross-term FMAs (2), TwoSum into the running
-# sum (6), two additions into the error word (2)
-FF_OPS_PER_FMA = 12
-
-
-def ff_peak_tflops(sm_mhz: float) -> float:
-    """Float-float FLOP/s the FP32 pipes can sustain: FP32 instructions per second /
-    FF_OPS_PER_FMA float-float multiply-adds, 2 flops each."""
-    return 148 * 128 * sm_mhz * 1e6 / FF_OPS_PER_FMA * 2 / 1e12
-
-
-SOLVE_KERNEL_SOURCES = ("gpv_init.cuh", "gpv_internal.h", "gpv_num.cuh", "gpv_solve.cu", "gpv_umma.cuh",
-                        "gpv_vartc.cu")
-
-
-def traffic_from_profiles(nvox_step: int):
-    """DRAM bytes per step of the solve kernels from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+def traffic_from_profiles(tall_flops_step: float):
+    """DRAM bytes of the tall-matrix launches of one step, from the committed ncu summary
+    (bytes per algorithmic flop of its voxels, captured on a smaller case), valid while the
+    kernel's sources match the summary's source_sha (else None)."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2410_17084_b300", "csrc")
     h = hashlib.sha256()
-    for f in SOLVE_KERNEL_SOURCES:  # the sources the solve kernels are compiled from
+    for f in ("gpv_tall.cu", "gpv_num.cuh", "gpv_umma.cuh", "gpv_internal.h", "gpv_common.cuh",
+              "gpv_init.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     sha = h.hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", "solve_ff_quadric_traffic.md")
+    path = os.path.join(ROOT, "profiles", "tall_stress_traffic.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_voxel:\s*([0-9.eE+]+)", txt)
+    m_b = re.search(r"dram_bytes_per_flop:\s*([0-9.eE+-]+)", txt)
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
-    return float(m_b.group(1)) * nvox_step
+    return float(m_b.group(1)) * tall_flops_step
 
 
+# ---- oracle comparison ------------------------------------------------------------------
+class ErrSample:
+    """A fixed, seeded sample of a workload's voxels, solved once by the FP64 oracle; the
+    GPU outputs of any leg on that workload are compared with it per output."""
+
+    def __init__(self, b, nsample=ERR_SAMPLE, seed=12345):
+        from oracle import compare
+        from oracle import oracle as O
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(b.nvox, size=min(nsample, b.nvox), replace=False))
+        self.idx = idx
+        self.b = b
+        self.sub = b.subset(idx)
+        t = time.perf_counter()
+        self.ref = compare.oracle_for_batch(self.sub)
+        self.ri = O.init_batch(self.ref["mean"], self.ref["var"], self.ref["axis"],
+                               self.sub.centres, self.sub.sf2, b.size, b.G, b.n_s, b.n_r)
+        self.seconds = time.perf_counter() - t
+
+    def errors(self, out) -> dict:
+        """out: device outputs of the whole workload (axis, mean, var, status[, pos, ...])."""
+        import torch
+        from oracle import compare
+        from oracle import oracle as O
+        it = torch.from_numpy(self.idx).to(out["mean"].device)
+        g = {k: out[k].index_select(0, it).cpu().numpy() for k in ("axis", "mean", "var", "status")}
+        ref = self.ref
+        ax = g["axis"].astype(np.int32)
+        diff = np.nonzero((ref["status"] == 0) & (ax != ref["axis"]) & (ax <= 2))[0]
+        if diff.size:  # axis-ambiguous voxels: the oracle takes the GPU's axis
+            ref = compare.oracle_for_batch(self.sub, gpu_axis=ax)
+        solved = (ref["status"] == 0) & ((g["status"].astype(np.uint32) & 0x55) == 0)
+        e = compare.gpr_errors(g["mean"], g["var"], ref, self.sub.sn2, solved)
+        res = {"sample_voxels": int(self.idx.size), "compared": e["n"],
+               "mean_max": e["mean_max"], "mean_p99": e["mean_p99"],
+               "var_max": e["var_max"], "var_p99": e["var_p99"],
+               "ambiguous_axis_reruns": int(diff.size)}
+        if "pos" in out:
+            ng = self.b.n_s * self.b.n_s
+            gi = (self.idx[:, None] * ng + np.arange(ng)[None, :]).reshape(-1)
+            gt = torch.from_numpy(gi).to(out["pos"].device)
+            ri = self.ri if not diff.size else O.init_batch(
+                ref["mean"], ref["var"], ref["axis"], self.sub.centres, self.sub.sf2,
+                self.b.size, self.b.G, self.b.n_s, self.b.n_r)
+            ie = compare.init_errors(out["pos"].index_select(0, gt).cpu().numpy(),
+                                     out["scale"].index_select(0, gt).cpu().numpy(),
+                                     out["quat"].index_select(0, gt).cpu().numpy(), ri,
+                                     valid=np.repeat(solved, ng))
+            res.update(scale_rel_max=ie["scale_rel_max"], rot_max=ie["rot_max"],
+                       unpinned_axes=ie["unpinned_axes"])
+        return res
+
+
+# ---- reference arm: the oracle on the host cores ------------------------------------------
 def run_reference(args, rank, world):
     """The FP64 CPU oracle timed on the host cores on a bounded sample of the workload."""
     from oracle import oracle as O
     from paper_2410_17084_b300 import synth
     if rank != 0:
         return
-    b = synth.quadric_batch()
+    b = synth.stress_batch()
     ncpu = os.cpu_count() or 1
-    # size one step to ~2 s of host work
-    probe = b.subset(np.arange(400))
+    rng = np.random.default_rng(99)
+    probe = b.subset(np.sort(rng.choice(b.nvox, 2000, replace=False)))
     t = time.perf_counter()
     O.solve_batch(probe.xyz, probe.offsets, probe.centres, probe.lam, probe.sf2, probe.sn2,
                   b.size, b.G, b.tau, nthreads=ncpu)
-    per = (time.perf_counter() - t) / 400
-    k = int(min(b.nvox, max(400, 2.0 / max(per, 1e-9))))
+    per = (time.perf_counter() - t) / probe.nvox
+    k = int(min(b.nvox, max(500, 4.0 / max(per, 1e-9))))  # about 4 s of host work per step
     times = []
     for s in range(args.warmup + args.steps):
-        idx = np.arange(s * k, (s + 1) * k) % b.nvox
+        idx = np.sort(rng.choice(b.nvox, k, replace=False))
         sub = b.subset(idx)
         t = time.perf_counter()
         r = O.solve_batch(sub.xyz, sub.offsets, sub.centres, sub.lam, sub.sf2, sub.sn2, b.size,
@@ -174,18 +250,20 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_voxels_per_step": k},
         "cpu_baseline": {"value": value, "unit": "voxel solves/s", "cores": ncpu,
-                         "kind": "oracle", "sample": f"{k} voxels of the workload per step"},
+                         "kind": "oracle",
+                         "sample": f"{k} voxels drawn at random from the workload per step"},
         "e2e": {"value": value, "unit": "voxel solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_leg(b, budget_s=12.0) -> dict:
-    """The oracle (GPR + Gaussian init) on all host cores over a bounded sample: a prefix
-    of the workload sized from a probe, or whole passes over it until about budget_s."""
+def cpu_baseline_leg(b, budget_s=15.0) -> dict:
+    """The oracle (GPR + Gaussian init) on all host cores over a bounded random sample of
+    the workload, sized from a probe to about budget_s."""
     from oracle import oracle as O
     ncpu = os.cpu_count() or 1
+    rng = np.random.default_rng(7)
 
     def one(sub):
         r = O.solve_batch(sub.xyz, sub.offsets, sub.centres, sub.lam, sub.sf2, sub.sn2, b.size,
@@ -193,109 +271,108 @@ def cpu_baseline_leg(b, budget_s=12.0) -> dict:
         O.init_batch(r["mean"], r["var"], r["axis"], sub.centres, sub.sf2, b.size, b.G, b.n_s,
                      b.n_r)
 
-    probe = b.subset(np.arange(min(b.nvox, 2000)))
+    probe = b.subset(np.sort(rng.choice(b.nvox, min(b.nvox, 1500), replace=False)))
     t = time.perf_counter()
     one(probe)
     per = (time.perf_counter() - t) / probe.nvox
     k = int(min(b.nvox, max(probe.nvox, budget_s / max(per, 1e-9))))
-    sub = b if k == b.nvox else b.subset(np.arange(k))
-    done, passes = 0, 0
+    sub = b.subset(np.sort(rng.choice(b.nvox, k, replace=False)))
     t = time.perf_counter()
-    while True:
-        one(sub)
-        done += k
-        passes += 1
-        dt = time.perf_counter() - t
-        if dt >= 0.8 * budget_s or k < b.nvox or passes >= 20:
-            break
-    what = (f"first {k} of {b.nvox} voxels" if k < b.nvox
-            else f"all {b.nvox} voxels x {passes} pass(es)")
-    return {"value": done / dt, "unit": "voxel solves/s", "cores": ncpu, "kind": "oracle",
-            "sample": f"{what} of the workload (GPR + Gaussian init)", "seconds": dt}
+    one(sub)
+    dt = time.perf_counter() - t
+    return {"value": k / dt, "unit": "voxel solves/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"{k} voxels drawn at random from the {b.nvox}-voxel workload "
+                      "(GPR + Gaussian init)", "seconds": dt}
 
 
-def run_extras(b, d, stream, timed) -> dict:
-    """Secondary legs: plain FP32 batched, the plain one-voxel-per-launch FP32 baseline,
-    the mixed-precision escalation workload (sample), the 1M-voxel stress workload as one
-    CUDA-graph replay, and serving at 10 Hz."""
+# ---- GPU legs ---------------------------------------------------------------------------
+def make_handle(gv, batch, prec, **kw):
+    cfg = gv.gp_voxels_config_default(voxel_size=batch.size, grid_side=batch.G,
+                                      n_s=batch.n_s, n_r=batch.n_r, tau=batch.tau,
+                                      max_points=int(max(256, batch.counts.max())),
+                                      max_voxels=batch.nvox, precision=prec, **kw)
+    return gv.GpVoxels(cfg)
+
+
+def solve_leg(gv, batch, dev, prec, timed, errs=None, steps=3, warmup=2, graph=True,
+              init=True):
+    g = make_handle(gv, batch, prec)
+    o = g.outputs(batch.nvox, "cuda", init=init)
+    f = lambda: g.solve_csr(dev["xyz"], dev["offsets"], dev["centres"], dev["lam"],
+                            dev["sf2"], dev["sn2"], out=o, init=init)
+    if graph:
+        gr = gv.capture_graph(f)
+        f = gr.replay
+    ms = timed(f, steps, warmup)
+    st = o["status"].cpu().numpy()
+    t = sum(ms) / len(ms)
+    res = {"value": batch.nvox / (t * 1e-3), "unit": "voxel solves/s", "ms_per_step": t,
+           "steps": steps, "predicted_pts_per_s": batch.nvox * batch.G * batch.G / (t * 1e-3),
+           "escalated": int(((st & gv.VOX_ESCALATED) != 0).sum())}
+    if errs is not None:
+        res["err"] = errs.errors(o)
+    g.close()
+    return res
+
+
+def run_extras(b5, errs5, timed, stream) -> dict:
+    """Secondary legs, each with its error against the oracle: plain FP32 on the headline
+    workload, the one-voxel-per-launch FP32 baseline, the escalation workload (200,000
+    voxels, G = 32) mixed and FP32, the 50,000-voxel quadric workload, the paper's Alg. 3
+    formulation, L_p, the rasteriser and serving at 10 Hz."""
     import torch
     from paper_2410_17084_b300 import gp_voxels as gv, serve, synth
     ex = {}
-
-    def solve_leg(batch, dev, prec, steps=3, warmup=3, graph=False, init=True):
-        cfg = gv.gp_voxels_config_default(voxel_size=batch.size, grid_side=batch.G,
-                                          n_s=batch.n_s, n_r=batch.n_r, tau=batch.tau,
-                                          max_points=int(max(256, batch.counts.max())),
-                                          max_voxels=batch.nvox, precision=prec)
-        g = gv.GpVoxels(cfg)
-        o = g.outputs(batch.nvox, "cuda", init=init)
-        # queued on the current stream, so that a graph capture records it
-        f = lambda: g.solve_csr(dev["xyz"], dev["offsets"], dev["centres"], dev["lam"],
-                                dev["sf2"], dev["sn2"], out=o, init=init)
-        if graph:
-            gr = gv.capture_graph(f)
-            f = gr.replay
-        ms = timed(f, steps, warmup)
-        st = o["status"].cpu().numpy()
-        g.close()
-        t = sum(ms) / len(ms)
-        return {"value": batch.nvox / (t * 1e-3), "unit": "voxel solves/s", "ms_per_step": t,
-                "predicted_pts_per_s": batch.nvox * batch.G * batch.G / (t * 1e-3),
-                "escalated": int(((st & gv.VOX_ESCALATED) != 0).sum())}
-
     try:
-        ex["fp32_batched"] = solve_leg(b, d, gv.PREC_FP32)
-        nsub = 5000
-        bs = b.subset(np.arange(nsub))
+        d5 = gv.batch_to_device(b5)
+        ex["stress1m_fp32"] = solve_leg(gv, b5, d5, gv.PREC_FP32, timed, errs5)
+        del d5
+        # one voxel per launch (plain FP32), on a random sample of the headline workload
+        rng = np.random.default_rng(5)
+        bs = b5.subset(np.sort(rng.choice(b5.nvox, 5000, replace=False)))
         ds = gv.batch_to_device(bs)
-        gsub = gv.GpVoxels(gv.gp_voxels_config_default(
-            voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau, max_points=256,
-            max_voxels=nsub, precision=gv.PREC_FP32))
-        osub = gsub.outputs(nsub, "cuda", init=True)
+        gsub = make_handle(gv, bs, gv.PREC_FP32, refine=0)
+        osub = gsub.outputs(bs.nvox, "cuda", init=True)
         mpl = timed(lambda: gsub.solve_csr(ds["xyz"], ds["offsets"], ds["centres"], ds["lam"],
                                            ds["sf2"], ds["sn2"], out=osub, init=True,
-                                           one_per_launch=True, stream=stream), 2, 1)
+                                           one_per_launch=True, stream=stream), 1, 1)
         gsub.close()
         tpl = sum(mpl) / len(mpl)
-        ex["fp32_one_voxel_per_launch"] = {"value": nsub / (tpl * 1e-3), "unit": "voxel solves/s",
-                                           "sample_voxels": nsub}
+        ex["fp32_one_voxel_per_launch"] = {
+            "value": bs.nvox / (tpl * 1e-3), "unit": "voxel solves/s",
+            "sample": "5,000 voxels drawn at random from the headline workload, one launch "
+                      "per voxel (plain FP32, no refinement)"}
     except Exception as e:  # an extra must not lose the headline
         ex["fp32_error"] = repr(e)
     try:
-        c3 = synth.mixed_batch(20000)
+        c3 = synth.mixed_batch()
+        e3 = ErrSample(c3)
         d3 = gv.batch_to_device(c3)
-        ex["mixed200k_sample"] = {
-            "workload": "first 20,000 of the 200,000-voxel escalation workload (counts "
-                        "power-law on [32,512], 10% collinear voxels, G = 32)",
-            "mixed": solve_leg(c3, d3, gv.PREC_MIXED, steps=2, warmup=1),
-            "fp32": solve_leg(c3, d3, gv.PREC_FP32, steps=2, warmup=1)}
+        ex["mixed200k"] = {
+            "workload": "200,000 voxels, counts power-law on [32,512], 10% collinear voxels "
+                        "(sn = 1e-4, Gram condition > 1e8), G = 32, fused init, one CUDA-graph "
+                        "replay per step",
+            "mixed": solve_leg(gv, c3, d3, gv.PREC_MIXED, timed, e3),
+            "fp32": solve_leg(gv, c3, d3, gv.PREC_FP32, timed, e3),
+            "oracle_seconds": e3.seconds}
         del d3
     except Exception as e:
         ex["mixed200k_error"] = repr(e)
     try:
-        c5 = synth.stress_batch(1000000)
-        d5 = gv.batch_to_device(c5)
-        ex["stress1m"] = {
-            "workload": "1,000,000 voxels, counts power-law on [4,1024], G = 9, fused "
-                        "Gaussian init, one CUDA-graph replay per step",
-            "fp32_graph": solve_leg(c5, d5, gv.PREC_FP32, steps=1, warmup=1, graph=True)}
-        s5 = c5.subset(np.arange(200000))
-        del d5
-        ds5 = gv.batch_to_device(s5)
-        ex["stress1m"]["mixed_graph_first200k"] = solve_leg(s5, ds5, gv.PREC_MIXED, steps=1,
-                                                            warmup=1, graph=True)
-        del ds5
-    except Exception as e:
-        ex["stress1m_error"] = repr(e)
-    try:  # the paper's Alg. 3 formulation with the full posterior covariance
-        import torch
+        c2 = synth.quadric_batch()
+        e2 = ErrSample(c2)
+        d2 = gv.batch_to_device(c2)
+        ex["quadric50k"] = {
+            "workload": "50,000 voxels, lognormal counts (median 64) clipped to [16,256], "
+                        "G = 16, fused init, one CUDA-graph replay per step",
+            "mixed": solve_leg(gv, c2, d2, gv.PREC_MIXED, timed, e2, steps=5),
+            "fp32": solve_leg(gv, c2, d2, gv.PREC_FP32, timed, e2, steps=5)}
+        # the paper's Alg. 3 formulation with the full posterior covariance
         na = 5000
-        ba = b.subset(np.arange(na))
+        ba = c2.subset(np.arange(na))
         da = gv.batch_to_device(ba)
-        ga = gv.GpVoxels(gv.gp_voxels_config_default(
-            voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau, max_points=256,
-            max_voxels=na))
-        Q = b.G * b.G
+        ga = make_handle(gv, ba, gv.PREC_MIXED)
+        Q = c2.G * c2.G
         oa = {"axis": torch.empty(na, dtype=torch.uint8, device="cuda"),
               "mean": torch.empty(na, Q, device="cuda"),
               "cov": torch.empty(na, Q, Q, device="cuda"),
@@ -309,41 +386,32 @@ def run_extras(b, d, stream, timed) -> dict:
         ga.close()
         ta = sum(ma) / len(ma)
         ex["alg3_full_covariance"] = {
-            "workload": f"first {na} voxels of the headline workload, the paper's Alg. 3 "
-                        "(FP32 LU + explicit inverse, full G^2 x G^2 Sigma* on tcgen05, "
-                        "3xTF32)",
+            "workload": f"first {na} voxels of the quadric workload, the paper's Alg. 3 (FP32 "
+                        "LU + explicit inverse, full G^2 x G^2 Sigma* on tcgen05, 3xTF32)",
             "value": na / (ta * 1e-3), "unit": "voxel solves/s", "ms_per_step": ta,
-            "sigma_bytes_per_step": na * Q * Q * 4,
             "sigma_GBps": na * Q * Q * 4 / (ta * 1e-3) / 1e9,
             "solved": int((st == 0).sum()), "too_large": int(((st & gv.VOX_TOO_LARGE) != 0).sum()),
             "nmax": nmax_a3}
         del da, oa
-    except Exception as e:
-        ex["alg3_error"] = repr(e)
-    try:  # structure similarity loss (Eq. 11): the scan's points against the Gaussians
-        import torch
-        gl = gv.GpVoxels(gv.gp_voxels_config_default(
-            voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau, max_points=256,
-            max_voxels=b.nvox))
-        ol = gl.solve_csr(d["xyz"], d["offsets"], d["centres"], d["lam"], d["sf2"], d["sn2"],
-                          init=True)
-        ok = torch.repeat_interleave((ol["status"] & 0x15) == 0, b.n_s * b.n_s)
+        # structure similarity loss (Eq. 11) and rasterisation (Eq. 9) of the Gaussians
+        gl = make_handle(gv, c2, gv.PREC_MIXED)
+        ol = gl.solve_csr(d2["xyz"], d2["offsets"], d2["centres"], d2["lam"], d2["sf2"],
+                          d2["sn2"], init=True)
+        ok = torch.repeat_interleave((ol["status"] & 0x15) == 0, c2.n_s * c2.n_s)
         gpos = ol["pos"][ok].contiguous()
         gsc = ol["scale"][ok].contiguous()
         m = int(gpos.shape[0])
-        npts = int(d["xyz"].shape[0])
+        npts = int(d2["xyz"].shape[0])
         lossd = torch.empty(1, dtype=torch.float64, device="cuda")
-        cell = b.size / b.n_s
-        fl = lambda: gv.gp_voxels_structure_loss(gl.h, gpos, gsc, m, d["xyz"], npts, cell, lossd)
+        cell = c2.size / c2.n_s
+        fl = lambda: gv.gp_voxels_structure_loss(gl.h, gpos, gsc, m, d2["xyz"], npts, cell, lossd)
         ml = timed(fl, 3, 2)
         tl = sum(ml) / len(ml)
         ex["structure_loss"] = {
-            "workload": f"L_p of Eq. 11: the {npts} points of the headline workload against "
-                        f"the {m} Gaussians initialised from it (hash grid, cell {cell} m)",
+            "workload": f"L_p of Eq. 11: the {npts} points of the quadric workload against the "
+                        f"{m} Gaussians initialised from it (hash grid, cell {cell} m)",
             "value": npts / (tl * 1e-3), "unit": "points/s", "ms_per_step": tl,
             "loss_m": float(lossd.item())}
-        # rasterisation (Eq. 9) of the same Gaussians from a camera 20 m above the lattice,
-        # looking down; seeded colours and opacities
         rng = np.random.default_rng(81)
         gq = ol["quat"][ok].contiguous()
         gop = torch.from_numpy(rng.uniform(0.2, 1.0, m).astype(np.float32)).cuda()
@@ -360,89 +428,96 @@ def run_extras(b, d, stream, timed) -> dict:
         mr = timed(fr, 3, 2)
         tr = sum(mr) / len(mr)
         ex["rasterize"] = {
-            "workload": f"{m} Gaussians (initialised from the headline workload, seeded colours "
+            "workload": f"{m} Gaussians (initialised from the quadric workload, seeded colours "
                         f"and opacities), one {W}x{H} camera 20 m above, colour + depth + "
                         "silhouette",
             "value": 1e3 / tr, "unit": "images/s", "ms_per_image": tr,
             "gaussians_per_s": m / (tr * 1e-3), "tile_pairs": pairs[-1],
             "covered": float((sil > 0).float().mean().item())}
         gl.close()
+        del d2
     except Exception as e:
-        ex["structure_loss_error"] = repr(e)
+        ex["quadric50k_error"] = repr(e)
     try:
-        scene = synth.lidar_scene()
-        nsc = 100
-        scans = [synth.lidar_scan(scene, k) for k in range(nsc)]
-        srv = serve.Server(serve.serving_config())
-        srv.run(scans[:3], realtime=False)  # first-use set-up of the kernels
-        srv2 = serve.Server(serve.serving_config())
-        lat, wall, _ = srv2.run(scans, arrivals=scene.arrivals[:nsc], realtime=True)
-        srv.close()
-        srv2.close()
-        # ALG.STORE alone: the inserts timed with events on their stream, scans one at a time
-        srv3 = serve.Server(serve.serving_config())
-        ln = srv3.lanes[0]
-        ins_ms, ins_pts = 0.0, 0
-        for k, scan in enumerate(scans):
-            npt = scan.shape[0]
-            ln.pin[:npt].copy_(torch.from_numpy(scan))
-            with torch.cuda.stream(ln.stream):
-                ln.xyz[:npt].copy_(ln.pin[:npt], non_blocking=True)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(ln.stream)
-                slot = gv.gp_voxels_insert_scan(srv3.g.h, ln.xyz, npt, k, ln.stream)
-                e1.record(ln.stream)
-                o = ln.out
-                gv.gp_voxels_solve(srv3.g.h, slot, o["axis"], o["mean"], o["var"], o["status"],
-                                   stream=ln.stream)
-                gv.gp_voxels_release_scan(srv3.g.h, slot, ln.stream)
-            ln.stream.synchronize()
-            ins_ms += e0.elapsed_time(e1)
-            ins_pts += npt
-        srv3.close()
-        ex["serving_insert"] = {
-            "workload": f"ALG.STORE of the same {nsc} scans into the device voxel store",
-            "points_per_s": ins_pts / (ins_ms * 1e-3),
-            "GBps": ins_pts * 32 / (ins_ms * 1e-3) / 1e9,
-            "bytes_per_point": "32 (12 point read + 12 bucket write + 8 key probe)",
-            "ms_per_scan": ins_ms / nsc}
-        # the same scans with the voxel state machine of Sec. 3.3 (eta = 0.3, variance
-        # feedback): each insert waits for the previous scan's solve
-        fcfg = serve.serving_config(eta=0.3, noise_floor=4e-6)
-        srv4 = serve.Server(fcfg)
-        srv4.run(scans[:3], realtime=False)
-        srv4.close()
-        srv5 = serve.Server(fcfg)
-        flat, fwall, _ = srv5.run(scans, arrivals=scene.arrivals[:nsc], realtime=True)
-        types = gv.gp_voxels_type_counts(srv5.g.h)
-        srv5.close()
-        ex["serving_state_machine"] = {
-            "workload": f"the same {nsc} scans, voxel types (a)-(d) with eta = 0.3 and variance "
-                        "feedback (noise floor 4e-6)",
-            "p50_ms": float(np.percentile(flat * 1e3, 50)),
-            "p99_ms": float(np.percentile(flat * 1e3, 99)),
-            "max_ms": float(flat.max() * 1e3), "scans_per_s": nsc / fwall,
-            "voxel_types_abcd": types}
-        ex["serving"] = {
-            "workload": f"{nsc} synthetic 64x1024 LiDAR scans, Poisson arrivals at 10 Hz, "
-                        "0.5 m voxels, 192-point buckets, G = 9, mixed precision + init",
-            "p50_ms": float(np.percentile(lat * 1e3, 50)),
-            "p99_ms": float(np.percentile(lat * 1e3, 99)),
-            "max_ms": float(lat.max() * 1e3), "scans_per_s": nsc / wall}
+        ex.update(serving_legs(gv, serve, synth))
     except Exception as e:
         ex["serving_error"] = repr(e)
     return ex
 
 
+def serving_legs(gv, serve, synth, nsc=None) -> dict:
+    """Serving at the LiDAR workload's configuration (Sec. 3.3, Alg. 2): 256-point buckets,
+    9 x 9 grid, 4 GB budget, scans arriving at 10 Hz (Poisson), checked against the oracle
+    on a sample of the rows of every 50th scan."""
+    import torch
+    from oracle import compare
+    nsc = nsc or int(os.environ.get("GPV_BENCH_SCANS", "600"))
+    scene = synth.lidar_scene()
+    scans = [synth.lidar_scan(scene, k) for k in range(nsc)]
+    cfg = serve.serving_config()
+    srv = serve.Server(cfg)
+    srv.run(scans[:3], realtime=False)  # first-use set-up of the kernels
+    srv.close()
+    srv2 = serve.Server(cfg)
+    lat, wall, _ = srv2.run(scans, arrivals=scene.arrivals[:nsc], realtime=True)
+    srv2.close()
+    # error: the first scans again, outputs collected, against the oracle's store and
+    # FP64 solve of the same points
+    nerr = 40
+    srv3 = serve.Server(cfg)
+    _, _, res = srv3.run(scans[:nerr], realtime=False, collect=True, max_inflight=1)
+    srv3.close()
+    errs = serving_oracle_err(gv, synth, cfg, scans[:nerr], res, every=8)
+    ex = {"serving": {
+        "workload": f"{nsc} synthetic 64x1024 LiDAR scans, Poisson arrivals at 10 Hz, 0.5 m "
+                    f"voxels, {cfg.max_points}-point buckets, G = 9, mixed precision + init, "
+                    f"{cfg.mem_budget >> 30} GB budget",
+        "scans": nsc, "p50_ms": float(np.percentile(lat * 1e3, 50)),
+        "p99_ms": float(np.percentile(lat * 1e3, 99)), "max_ms": float(lat.max() * 1e3),
+        "scans_per_s": nsc / wall, "err": errs}}
+    return ex
+
+
+def serving_oracle_err(gv, synth, cfg, scans, res, every=8) -> dict:
+    """The oracle's store (Alg. 2) fed the same scans in order; every `every`-th scan's rows
+    solved by the FP64 oracle from the points it holds and compared with the served rows."""
+    from oracle import compare
+    from oracle import oracle as O
+    store = O.VoxelStore(cfg.voxel_size, cfg.max_points)
+    mm, vm, nrow = 0.0, 0.0, 0
+    for k, scan in enumerate(scans):
+        touched = store.insert_scan(scan)
+        if k % every:
+            continue
+        r = res[k]
+        pts = [store.points(t) for t in touched]
+        counts = np.array([q.shape[0] for q in pts], dtype=np.int64)
+        off = np.zeros(len(pts) + 1, np.int64)
+        off[1:] = np.cumsum(counts)
+        nv = len(pts)
+        cen = O.voxel_centres(np.array(touched, np.int32), cfg.voxel_size)
+        b = synth.VoxelBatch("scan", np.concatenate(pts).astype(np.float32), off, cen,
+                             np.full(nv, cfg.lambda_, np.float32), np.full(nv, cfg.sf2, np.float32),
+                             np.full(nv, cfg.sn2, np.float32), cfg.voxel_size, cfg.grid_side,
+                             cfg.n_s, cfg.n_r, cfg.tau, counts, np.zeros(nv, bool))
+        ax = r["axis"].astype(np.int32)
+        ref = compare.oracle_for_batch(b, gpu_axis=np.where(ax <= 2, ax, -1))
+        solved = (ref["status"] == 0) & ((r["status"].astype(np.uint32) & 0x55) == 0)
+        e = compare.gpr_errors(r["mean"], r["var"], ref, b.sn2, solved)
+        mm, vm, nrow = max(mm, e["mean_max"]), max(vm, e["var_max"]), nrow + e["n"]
+    return {"mean_max": mm, "var_max": vm, "rows_compared": nrow,
+            "sample": f"every {every}th of the first {len(scans)} scans, every solved row, "
+                      "against the oracle's store and FP64 solve of the same points"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip FP32 / one-per-launch legs")
+    ap.add_argument("--no-extras", action="store_true", help="headline leg only")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -464,28 +539,32 @@ def main():
     if dist is not None:
         dist.barrier()
 
-    b = synth.quadric_batch(seed=D.rank_seed(1, rank))  # independent batch per rank
+    b = synth.stress_batch(seed=D.rank_seed(4, rank))  # independent batch per rank
     G = b.G
-    flops = algorithmic_flops(b.counts, G)
     d = gv.batch_to_device(b)
-    cfg = gv.gp_voxels_config_default(voxel_size=b.size, grid_side=G, n_s=b.n_s, n_r=b.n_r,
-                                      tau=b.tau, max_points=256, max_voxels=b.nvox,
-                                      precision=gv.PREC_MIXED, mean_mode=1)
-    g = gv.GpVoxels(cfg)
-    tuned = g.autotune(d["xyz"], d["offsets"], d["centres"], d["lam"], d["sf2"], d["sn2"])
-    # measured arithmetic peaks (FP32 FMA, float-float multiply-add), outside the timed region
-    meas_fp32 = gv.gp_voxels_measure_peak(0)
+    g = make_handle(gv, b, gv.PREC_MIXED, mean_mode=1)
+    plan = gv.gp_voxels_plan_info(g.h)
+    fl = split_flops(b.counts, G, plan)
+    # autotune the shared-memory buckets on a 100,000-voxel prefix (same count distribution)
+    pre = b.subset(np.arange(100000))
+    dp = gv.batch_to_device(pre)
+    tuned = g.autotune(dp["xyz"], dp["offsets"], dp["centres"], dp["lam"], dp["sf2"], dp["sn2"])
+    del dp
     meas_ff = gv.gp_voxels_measure_peak(1)
+    peaks = measured_peaks()
     out = g.outputs(b.nvox, "cuda", init=True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step(handle=g, o=out, flags=0):
-        gv.gp_voxels_solve_csr(handle.h, d["xyz"], d["offsets"], b.nvox, d["centres"], d["lam"],
-                               d["sf2"], d["sn2"], o["axis"], o["mean"], o["var"], o["status"],
-                               o.get("pos"), o.get("scale"), o.get("quat"), flags, stream)
+    def step():
+        gv.gp_voxels_solve_csr(g.h, d["xyz"], d["offsets"], b.nvox, d["centres"], d["lam"],
+                               d["sf2"], d["sn2"], out["axis"], out["mean"], out["var"],
+                               out["status"], out["pos"], out["scale"], out["quat"], 0,
+                               torch.cuda.current_stream())
 
-    def timed(fn, steps, warmup):
+    tall_ms = []
+
+    def timed(fn, steps, warmup, tall=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
@@ -498,45 +577,41 @@ def main():
             fn()
             e1.record(stream)
             evs.append((e0, e1))
+            if tall is not None:  # the tall-matrix launches of this step (events on their stream)
+                tall.append(gv.gp_voxels_last_tall_ms(g.h))
         torch.cuda.synchronize()
         return [a.elapsed_time(c) for a, c in evs]
 
+    gv.gp_voxels_set_timing(g.h, True)
+    graph = gv.capture_graph(step)
+    launches = gv.gp_voxels_last_launches(g.h)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms = timed(step, args.steps, args.warmup)
+        ms = timed(graph.replay, args.steps, args.warmup, tall=tall_ms)
     t_step = D.max_over_ranks(sum(ms) / len(ms), dist, "cuda")
     value = world * b.nvox / (t_step * 1e-3)
     st = out["status"].cpu().numpy()
     n_esc = int(((st & gv.VOX_ESCALATED) != 0).sum())
-    launches = gv.gp_voxels_last_launches(g.h)
+    errs5 = ErrSample(b) if rank == 0 else None
+    err = errs5.errors(out) if rank == 0 else None
 
     # ---- e2e: host buffers in, host buffers out, through the C ABI ------------------
     pin = {k: torch.from_numpy(getattr(b, k)).pin_memory() for k in
            ("xyz", "offsets", "centres", "lam", "sf2", "sn2")}
-    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
     h2d = sum(v.numel() * v.element_size() for v in pin.values())
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
-
-    def e2e_step():
-        for k, v in pin.items():
-            d[k].copy_(v, non_blocking=True)
-        step()
-        for k, v in out.items():
-            host_out[k].copy_(v, non_blocking=True)
-
-    e2e_ms = timed(e2e_step, max(3, args.steps // 2), 3)
-    t_e2e_serial = D.max_over_ranks(sum(e2e_ms) / len(e2e_ms), dist, "cuda")
-
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
     # Streamed: two sets of device inputs and outputs; every step copies its inputs in and
-    # its outputs out (pinned host memory), on copy streams of their own, so the copies of
+    # its outputs out (pinned host memory) on copy streams of their own, so the copies of
     # one step overlap the neighbouring steps' solves.  Timed from the first input copy to
     # the last output copy.
     d2 = {k: torch.empty_like(v) for k, v in d.items()}
     dsets, osets = [d, d2], [out, g.outputs(b.nvox, "cuda", init=True)]
-    hsets = [host_out, {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}]
+    hsets = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+             for _ in range(2)]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    gv.gp_voxels_set_timing(g.h, False)
 
     def e2e_stream(nsteps):
         ev_in = [torch.cuda.Event() for _ in range(2)]
@@ -557,7 +632,6 @@ def main():
             stream.wait_event(ev_in[j])
             if k >= 2:
                 stream.wait_event(ev_out[j])  # the outputs of step k - 2 are read out
-            flush.fill_(1.0)
             o, dd = osets[j], dsets[j]
             gv.gp_voxels_solve_csr(g.h, dd["xyz"], dd["offsets"], b.nvox, dd["centres"],
                                    dd["lam"], dd["sf2"], dd["sn2"], o["axis"], o["mean"],
@@ -573,15 +647,26 @@ def main():
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / nsteps
 
-    e2e_stream(3)  # warm-up
+    e2e_stream(2)  # warm-up
     t_e2e = D.max_over_ranks(e2e_stream(max(3, args.steps)), dist, "cuda")
+    del d2, dsets, osets, hsets
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = run_extras(b, d, stream, timed)
+        extras = run_extras(b, errs5, timed, stream)
     clocks = clk.summary()
-    peak_ff = ff_peak_tflops(2032.0)
-    achieved = flops / (t_step * 1e-3) / 1e12
+
+    # ---- roofline ---------------------------------------------------------------------
+    # dominant kernel: the tall-matrix launches (events around them on their own stream)
+    t_tall = sum(tall_ms) / max(len(tall_ms), 1)
+    bf16 = peaks["bf16_tflops_sustained"]
+    p_tc = bf16 / SLICE_PAIRS         # float-float-accurate products on the tensor cores
+    p_ff = meas_ff                     # measured float-float multiply-add rate, CUDA cores
+    tall_floor_ms = 1e3 * (fl["tall_tc"] / (p_tc * 1e12) + fl["tall_ff"] / (p_ff * 1e12))
+    tall_peak = fl["tall_total"] / (tall_floor_ms * 1e-3) / 1e12
+    tall_ach = fl["tall_total"] / (t_tall * 1e-3) / 1e12 if t_tall > 0 else 0.0
+    step_floor_ms = 1e3 * (fl["tc"] / (p_tc * 1e12) + fl["ff"] / (p_ff * 1e12))
+    step_ach = fl["total"] / (t_step * 1e-3) / 1e12
     line = {
         "metric": METRIC,
         "value": value,
@@ -596,32 +681,40 @@ def main():
         "dtype": "f32x2",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "voxels_per_gpu": b.nvox, "grid": f"{G}x{G}",
-                   "precision": "mixed (float-float + FP64 escalation)",
-                   "l2": "flushed between timed steps (256 MiB write)",
-                   "autotune": f"CTA size per size bucket chosen by gp_voxels_autotune "
-                               f"({tuned} of the default choices changed)",
+                   "precision": "mixed (float-float + exact BF16 slice products + FP64 "
+                                "escalation)",
+                   "l2": "flushed between timed steps (256 MiB write); inputs 0.76 GB > L2",
+                   "autotune": f"CTA size per shared-memory size bucket chosen by "
+                               f"gp_voxels_autotune on a 100,000-voxel prefix ({tuned} changed)",
+                   "plan": plan,
                    "parallelism": f"independent batches per GPU x{world}"},
         "predicted_pts_per_s": value * G * G,
         "escalated_voxels": n_esc,
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ff, "unit": "TFLOP/s",
-                     "frac": achieved / peak_ff, "traffic": traffic_from_profiles(b.nvox),
-                     "peak_note": "float-float FLOP/s of the FP32 pipes: 148 SMs x 128 lanes x "
-                                  "2032 MHz FP32 instructions/s / 12 per float-float "
-                                  "multiply-add x 2 flops (derived from unit counts and the "
-                                  "maximum clock); achieved = algorithmic FLOPs of the step "
-                                  "(n^3/3 + n^2 G^2 + 4 n G^2 + 4 n^2 per voxel) / step time, "
-                                  "the solve kernels of all size buckets running concurrently, "
-                                  "then the tensor-core variance kernel (its BF16 slice "
-                                  "products are not counted: only the algorithmic FLOPs are)",
-                     "measured_fp32_tflops": meas_fp32,
-                     "measured_ff_tflops": meas_ff,
-                     "frac_of_measured_ff": achieved / meas_ff},
+        "err": err,
+        "roofline": {
+            "bound": "tensor", "achieved": tall_ach, "peak": tall_peak, "unit": "TFLOP/s",
+            "frac": tall_ach / tall_peak if tall_peak else None,
+            "traffic": traffic_from_profiles(fl["tall_total"]),
+            "kernel": "k_tall (tall-matrix factorisation of the voxels with more than "
+                      f"{plan['tall_min']} points: {fl['tall_voxels']} voxels, "
+                      f"{fl['tall_total'] / 1e12:.3f} TFLOP algorithmic per step)",
+            "kernel_ms": t_tall,
+            "peak_note": "composite floor of the kernel's algorithmic work by the unit that "
+                         "runs it: the panel updates as exact BF16 slice products at the "
+                         f"measured sustained BF16 rate / {SLICE_PAIRS} slice products per "
+                         f"float-float product ({bf16} / {SLICE_PAIRS} = {p_tc:.1f} TFLOP/s), "
+                         "the in-panel work (32 flops per row and column) at the measured "
+                         f"float-float rate ({p_ff:.2f} TFLOP/s); peak = its work / that "
+                         "floor (of measured)",
+            "step": {"achieved": step_ach, "floor_ms": step_floor_ms,
+                     "peak": fl["total"] / (step_floor_ms * 1e-3) / 1e12,
+                     "frac": step_floor_ms / t_step,
+                     "tc_tflop": fl["tc"] / 1e12, "ff_tflop": fl["ff"] / 1e12}},
         "e2e": {"value": world * b.nvox / (t_e2e * 1e-3), "unit": "voxel solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "mode": "streamed: two device input/output sets, host-device copies on "
-                        "their own streams overlapping the neighbouring steps' solves",
-                "serial_value": world * b.nvox / (t_e2e_serial * 1e-3)},
+                        "their own streams overlapping the neighbouring steps' solves"},
         "clocks": clocks,
     }
     line.update(extras)

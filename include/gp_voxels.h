@@ -429,6 +429,23 @@ GPV_API int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int64_t
  * handle queued (a diagnostic; the paper has no counterpart).  Errors: GPV_EINVAL. */
 GPV_API int gp_voxels_last_launches(const gp_voxels_t* h, int32_t* h_kernels);
 
+/* Launch plan of this handle (a diagnostic; the paper has no counterpart):
+ * h_info[0] = tall_min (voxels with more points take the tall-matrix tensor-core path; -1:
+ * the path is off), [1] = largest n of the tensor-core variance with the factor in shared
+ * memory (0: off), [2] = largest n of the shared-memory solve kernels, [3] = size buckets.
+ * Errors: GPV_EINVAL. */
+GPV_API int gp_voxels_plan_info(const gp_voxels_t* h, int32_t* h_info);
+
+/* Device time of the tall-matrix launches of this handle's batch solves (a diagnostic for
+ * roofline measurement; the paper has no counterpart).  gp_voxels_set_timing(h, 1) makes
+ * every later gp_voxels_solve_csr record CUDA events on the stream of those launches
+ * around them (also inside a stream capture: the records become part of the graph);
+ * gp_voxels_last_tall_ms waits for the last recorded end event and returns the elapsed
+ * milliseconds (0 when the last solve had no tall-matrix voxels).  Errors: GPV_EINVAL,
+ * GPV_ECUDA. */
+GPV_API int gp_voxels_set_timing(gp_voxels_t* h, int32_t on);
+GPV_API int gp_voxels_last_tall_ms(gp_voxels_t* h, float* h_ms);
+
 /* Arithmetic peak of this GPU measured with the solve's own arithmetic (the paper has no
  * counterpart; a reference for roofline fractions): kind 0 = FP32 fused multiply-add, kind 1
  * = the float-float accumulate-form multiply-add of the variance contraction; 2 flops per

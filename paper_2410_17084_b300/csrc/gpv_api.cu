@@ -108,6 +108,9 @@ struct gp_voxels {
     int gws_grid = 0;
     int tall_min = INT_MAX;         // voxels with more points take the tall-matrix path
     int64_t tall_stride = 0;        // bytes of one CTA's slice store
+    bool timing = false;            // record events around the tall-matrix launches
+    bool timed_tall = false;        // the last batch solve recorded them
+    cudaEvent_t ev_tall[2] = {nullptr, nullptr};
     int esc_grid_small = 0, esc_smem_small = 0, esc_grid_big = 0, esc_smem_big = 0;
     size_t bytes = 0;
     gpv_store* store = nullptr;
@@ -429,6 +432,8 @@ static void release(gp_voxels_t* h)
         delete[] h->sctx;
     }
     cudaFree(h->d_one); cudaFree(h->d_ident); cudaFree(h->d_pl_next);
+    for (auto& e : h->ev_tall)
+        if (e) cudaEventDestroy(e);
     cudaFree(h->a3.pb); cudaFree(h->a3.ps); cudaFree(h->a3.fa); cudaFree(h->a3.fb);
     cudaFree(h->a3.st); cudaFree(h->a3.n);
     cudaFree(h->lp.keys); cudaFree(h->lp.head); cudaFree(h->lp.next); cudaFree(h->lp.pending);
@@ -628,6 +633,17 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     return a;
 }
 
+// An event record that also works inside a stream capture (it then becomes a node of the
+// graph, recorded at every replay).
+static cudaError_t record_event(cudaEvent_t e, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(s, &cs);
+    if (r != cudaSuccess) return r;
+    return cudaEventRecordWithFlags(e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                                : cudaEventRecordDefault);
+}
+
 static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
                            const int64_t* d_offsets, int32_t nvox, const int32_t* d_nvox,
                            const float* d_centres, const float* d_lambda, const float* d_sf2,
@@ -685,6 +701,8 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
     // one after another on the first side stream.
     CK(cudaEventRecord(x.ev_fork, s));
     int used = 0;
+    bool timed = false;               // events around the tall-matrix launches recorded
+    cudaStream_t tall_ss = nullptr;
     for (int b = P.nb - 1; b >= 0; --b) {
         const Bucket& B = P.b[b];
         const bool tcv = a.tc_ws && B.tcv_ok;  // the variant, factor in shared memory
@@ -697,7 +715,12 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_next = x.d_next + b;
         a.nmax = (B.tri_smem || tcv) ? B.hi : c.max_points;
         if (B.tall && x.d_tall && !a.pvar) {  // large voxels: the tall-matrix factorisation
+            if (h->timing && &x == &h->main && !timed) {
+                CK(record_event(h->ev_tall[0], ss));
+                timed = true;
+            }
             CK(launch_tall(kind, a, x.d_tall, h->tall_stride, (B.hi + 31) / 32 * 32, h->sms, ss));
+            tall_ss = ss;
         } else if (tcv) {  // the variance goes to the tensor cores
             a.percol_max = B.v.percol ? B.hi : 0;
             a.panel = B.v.panel;
@@ -721,6 +744,8 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         ++h->last_launches;
         used |= 1 << (si % kNumBuckets);
     }
+    if (timed) CK(record_event(h->ev_tall[1], tall_ss));
+    if (&x == &h->main) h->timed_tall = timed;
     for (int i = 0; i < kNumBuckets; ++i)
         if (used & (1 << i)) {
             CK(cudaEventRecord(x.ev_join[i], x.side[i]));
@@ -1246,6 +1271,39 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *h_changed = changed;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_plan_info(const gp_voxels_t* h, int32_t* h_info)
+{
+    if (!h || !h_info) return GPV_EINVAL;
+    const PrecPlan& P = h->plan[prec_kind(h->cfg.precision)];
+    h_info[0] = h->tall_min == INT_MAX ? -1 : h->tall_min;
+    h_info[1] = P.tc_nmax;
+    h_info[2] = P.nmax_smem;
+    h_info[3] = P.nb;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_set_timing(gp_voxels_t* h, int32_t on)
+{
+    if (!h) return GPV_EINVAL;
+    if (on && !h->ev_tall[0]) {
+        CK(cudaEventCreate(&h->ev_tall[0]));
+        CK(cudaEventCreate(&h->ev_tall[1]));
+    }
+    h->timing = on != 0;
+    h->timed_tall = false;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_last_tall_ms(gp_voxels_t* h, float* h_ms)
+{
+    if (!h || !h_ms) return GPV_EINVAL;
+    *h_ms = 0.f;
+    if (!h->timed_tall || !h->ev_tall[0]) return GPV_OK;
+    CK(cudaEventSynchronize(h->ev_tall[1]));
+    CK(cudaEventElapsedTime(h_ms, h->ev_tall[0], h->ev_tall[1]));
     return GPV_OK;
 }
 

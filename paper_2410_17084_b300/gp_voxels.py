@@ -31,7 +31,8 @@ EXPORTED = [
     "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
     "gp_voxels_scan_types", "gp_voxels_type_counts", "gp_voxels_solve_alg3",
     "gp_voxels_structure_loss", "gp_voxels_render", "gp_voxels_measure_peak",
-    "gp_voxels_selftest_bounded_wait",
+    "gp_voxels_selftest_bounded_wait", "gp_voxels_plan_info", "gp_voxels_set_timing",
+    "gp_voxels_last_tall_ms",
 ]
 NOALLOC_MAX_VOXELS = 65536
 
@@ -126,6 +127,9 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.c_int32, P, P, P, P, P, P, P, P, P,
                                                   P, P, P]
         L.gp_voxels_last_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        L.gp_voxels_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        L.gp_voxels_set_timing.argtypes = [P, ctypes.c_int32]
+        L.gp_voxels_last_tall_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
         L.gp_voxels_autotune.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P, P, P, P, P, P,
                                          P, P, ctypes.POINTER(ctypes.c_int32)]
         # h, xyz, offsets, nvox, centres, lam, sf2, sn2, noise, axis, mean, var, status,
@@ -353,6 +357,22 @@ def gp_voxels_last_launches(h) -> int:
     n = ctypes.c_int32()
     _check("gp_voxels_last_launches", lib().gp_voxels_last_launches(h, ctypes.byref(n)))
     return n.value
+
+
+def gp_voxels_plan_info(h) -> dict:
+    a = (ctypes.c_int32 * 4)()
+    _check("gp_voxels_plan_info", lib().gp_voxels_plan_info(h, a))
+    return {"tall_min": a[0], "tc_nmax": a[1], "nmax_smem": a[2], "buckets": a[3]}
+
+
+def gp_voxels_set_timing(h, on: bool) -> None:
+    _check("gp_voxels_set_timing", lib().gp_voxels_set_timing(h, 1 if on else 0))
+
+
+def gp_voxels_last_tall_ms(h) -> float:
+    ms = ctypes.c_float()
+    _check("gp_voxels_last_tall_ms", lib().gp_voxels_last_tall_ms(h, ctypes.byref(ms)))
+    return ms.value
 
 
 def gp_voxels_store_voxels(h) -> int:

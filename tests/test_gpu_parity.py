@@ -173,11 +173,12 @@ def test_empty_batch(gpv):
 def test_one_per_launch_equals_batched(gpv):
     """The baseline (one launch per voxel) runs the same per-voxel code: outputs agree
     bit for bit with the batched persistent launch when that forms the variance in the
-    solve kernel too (tensor-core variance off; the baseline has no workspace for it)."""
+    solve kernel too (tensor-core variance and tall-matrix path off; the baseline has no
+    workspace for either)."""
     from paper_2410_17084_b300 import synth
     b = synth.quadric_batch(400, seed=11)
     for prec in (0, 1):
-        a = _run(gpv, b, prec, tc_workspace_mb=0)
+        a = _run(gpv, b, prec, tc_workspace_mb=0, tall_min_points=-1)
         c = _run(gpv, b, prec, one_per_launch=True)
         if prec == 1:  # escalated voxels are solved in FP64 only on the batched path
             keep = (a["status"] & 2) == 0
