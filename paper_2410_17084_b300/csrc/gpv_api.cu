@@ -384,7 +384,8 @@ static TcSplit tc_split(const gp_voxels_config* c, int Gp, size_t rest)
 static size_t solve_bytes(const gp_voxels_config* c, int sms, int Gp)
 {
     size_t b = ctx_bytes(c, c->max_voxels, sms, Gp);
-    b += tall_bytes(c, sms, Gp);
+    // the batch entry and every scan slot have a slice store of the tall-matrix path
+    b += tall_bytes(c, sms, Gp) * (size_t)(1 + (c->hash_capacity > 0 ? c->scan_slots : 0));
     b += sizeof(int32_t) * ((size_t)c->max_voxels * 2 + 1);  // ident, per-launch counters
     if (c->hash_capacity > 0)
         b += (size_t)c->scan_slots * ctx_bytes(c, c->max_scan_voxels, sms, Gp);
@@ -533,12 +534,20 @@ static int create_impl(gp_voxels_t* h)
         if (e != cudaSuccess) return cuda_fail(e);
         h->bytes += b;
     }
+    const size_t tall_slot = h->tall_min != INT_MAX ? (size_t)h->sms * (size_t)h->tall_stride : 0;
     if (need_tc.main > 0 || (c.hash_capacity > 0 && need_tc.slot > 0)) CK(var_tc_prepare());
     if (c.hash_capacity > 0) {
         h->sctx = new (std::nothrow) SolveCtx[c.scan_slots];
         if (!h->sctx) return GPV_ENOMEM;
-        for (int i = 0; i < c.scan_slots; ++i)
+        for (int i = 0; i < c.scan_slots; ++i) {
             if ((rc = ctx_create(h, h->sctx[i], c.max_scan_voxels, need_tc.slot)) != GPV_OK) return rc;
+            if (tall_slot) {
+                cudaError_t e = cudaMalloc((void**)&h->sctx[i].d_tall, tall_slot);
+                if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return GPV_ENOMEM; }
+                if (e != cudaSuccess) return cuda_fail(e);
+                h->bytes += tall_slot;
+            }
+        }
     }
     const int one = 1;
     CK(cudaMemcpy(h->d_one, &one, sizeof(int), cudaMemcpyHostToDevice));
@@ -629,6 +638,8 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.tc_off_v = x.d_tc_off_v;
         a.tc_nmax = h->plan[PREC_FF].tc_nmax;
         a.tc_nmax_gl = h->plan[PREC_FF].tc_nmax_gl;
+        // voxels of the tall-matrix path form their variance themselves
+        if (x.d_tall) a.tc_nmax_gl = std::min(a.tc_nmax_gl, h->tall_min);
     }
     return a;
 }

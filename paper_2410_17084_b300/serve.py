@@ -134,11 +134,10 @@ class Server:
 
 def serving_config(**overrides) -> gv.gp_voxels_config:
     """The LiDAR serving workload: 0.5 m voxels, 9 x 9 query grid (n_s = n_r = 3),
-    tau = 10, 192 points per bucket (the largest voxel whose factor, in the 8-byte
-    precisions, stays in one SM's shared memory at this grid: larger buckets take the
-    global-memory workspace path, about three times slower per point), lengthscale 0.2 m
-    (lambda 12.5), sn 0.02 m, a 4 GB memory budget."""
-    d = dict(voxel_size=0.5, grid_side=9, n_s=3, n_r=3, tau=10, max_points=192,
+    tau = 10, 256 points per bucket (voxels beyond the shared-memory kernels take the
+    tall-matrix tensor-core path, which every scan slot has a slice store for),
+    lengthscale 0.2 m (lambda 12.5), sn 0.02 m, a 4 GB memory budget."""
+    d = dict(voxel_size=0.5, grid_side=9, n_s=3, n_r=3, tau=10, max_points=256,
              max_voxels=1 << 16, precision=gv.PREC_MIXED, hash_capacity=1 << 19,
              mem_budget=4 << 30, scan_slots=4, max_scan_points=1 << 17,
              max_scan_voxels=1 << 15, snap_points=1 << 21, lambda_=12.5, sf2=1.0, sn2=4e-4)
