@@ -286,7 +286,21 @@ def cpu_baseline_leg(b, budget_s=15.0) -> dict:
 
 
 # ---- GPU legs ---------------------------------------------------------------------------
+def tc_workspace_mb(batch, nmax=224) -> int:
+    """MiB of tensor-core variance workspace a batch needs (the handle's per-voxel hand-over
+    of L^-1, the node factors and the means, float-float): every voxel that takes the
+    tensor-core variance gets its own slice, so a batch of a million voxels needs more
+    than the 4 GiB default."""
+    G = batch.G
+    Gp = (G + 3) // 4 * 4
+    n = batch.counts[(batch.counts <= nmax) & (batch.counts >= batch.tau)].astype(np.int64)
+    e = n * (n + 1) // 2 + n * G + n * Gp + 2 * G * G
+    need = int(np.sum((8 * e + 4 * (n + G * G) + 15) // 16 * 16))
+    return max(4096, (need >> 20) + 256)
+
+
 def make_handle(gv, batch, prec, **kw):
+    kw.setdefault("tc_workspace_mb", tc_workspace_mb(batch))
     cfg = gv.gp_voxels_config_default(voxel_size=batch.size, grid_side=batch.G,
                                       n_s=batch.n_s, n_r=batch.n_r, tau=batch.tau,
                                       max_points=int(max(256, batch.counts.max())),

@@ -62,8 +62,11 @@ struct PrecPlan {
     int nmax_smem = 0;
     int tc_nmax = 0;      // largest n of the tensor-core variance (0: off)
     int tc_nmax_gl = 0;   // the same for the global-workspace buckets
-    bool fb_tri = true;   // the re-solve launch keeps the factor in shared memory
-    int fb_smem = 0, fb_grid = 0;  // regular re-solve of what the variant could not hand over
+    // regular re-solve of what the variant could not hand over: voxels up to nmax_smem in
+    // shared memory, larger ones with the factor in the global workspace (or, where the
+    // context has one, on the tall-matrix path)
+    int fb_smem = 0, fb_grid = 0, fb_nthr = 512;
+    int fbb_smem = 0, fbb_grid = 0;
 };
 
 // Work queues, workspace and streams of one solve in flight.  The CSR entry owns one;
@@ -262,14 +265,17 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
             if (occ < 1) return GPV_EINVAL;
             B.v.grid = h->sms * occ;
         }
-        // the re-solve of what the variant cannot hand over: in shared memory if the regular
-        // plan fits its largest n, else with the factor in the global workspace
-        P.fb_tri = P.tc_nmax <= P.nmax_smem;
-        P.fb_smem = smem_plan(P.fb_tri ? P.tc_nmax : c.max_points, c.grid_side, h->Gp, 8, P.fb_tri, 512).total;
+        // the re-solve of what the variant cannot hand over
+        P.fb_nthr = solve_threads(P.nmax_smem, true);
+        P.fb_smem = smem_plan(P.nmax_smem, c.grid_side, h->Gp, 8, true, P.fb_nthr).total;
         int occ = 0;
-        CK(solve_occupancy(kind, P.fb_tri, 512, P.fb_smem, &occ));
+        CK(solve_occupancy(kind, true, P.fb_nthr, P.fb_smem, &occ));
         if (occ < 1) return GPV_EINVAL;
-        P.fb_grid = P.fb_tri ? h->sms * occ : h->gws_grid;
+        P.fb_grid = h->sms * occ;
+        P.fbb_smem = smem_plan(c.max_points, c.grid_side, h->Gp, 8, false, 512).total;
+        CK(solve_occupancy(kind, false, 512, P.fbb_smem, &occ));
+        if (occ < 1) return GPV_EINVAL;
+        P.fbb_grid = h->gws_grid;
     }
     CK(cudaMalloc(&P.d_hi, sizeof(int) * kNumBuckets));
     CK(cudaMemcpy(P.d_hi, hi_host, sizeof(int) * P.nb, cudaMemcpyHostToDevice));
@@ -345,7 +351,7 @@ static size_t ctx_bytes(const gp_voxels_config* c, int cap, int sms, int Gp)
 // Queue lists of the tensor-core variance for a context of cap voxels.
 static size_t tc_lists(int cap)
 {
-    return (size_t)cap * (2 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
+    return (size_t)cap * (3 * sizeof(int32_t) + 2 * sizeof(int64_t)) + sizeof(TcCounters) +
            sizeof(int32_t) * kNumBuckets;
 }
 
@@ -472,7 +478,7 @@ static int ctx_create(gp_voxels_t* h, SolveCtx& x, int cap, size_t tc_total = 0)
         AL(x.d_tc, sizeof(TcCounters));
         AL(x.d_tc_v, sizeof(int32_t) * (size_t)cap);
         AL(x.d_tc_off, sizeof(int64_t) * (size_t)cap);
-        AL(x.d_tc_fb, sizeof(int32_t) * (size_t)cap);
+        AL(x.d_tc_fb, sizeof(int32_t) * (size_t)cap * 2);
         AL(x.d_tc_off_v, sizeof(long long) * (size_t)cap);
         AL(x.d_tc_next, sizeof(int32_t) * kNumBuckets);
     }
@@ -635,6 +641,7 @@ static SolveArgs make_args(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.tc_v = x.d_tc_v;
         a.tc_off = x.d_tc_off;
         a.tc_fb = x.d_tc_fb;
+        a.fb_nsmall = h->plan[PREC_FF].nmax_smem;
         a.tc_off_v = x.d_tc_off_v;
         a.tc_nmax = h->plan[PREC_FF].tc_nmax;
         a.tc_nmax_gl = h->plan[PREC_FF].tc_nmax_gl;
@@ -770,11 +777,24 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
             f.work_base = nullptr;
             f.work_count = &a.tc->fb_count;
             f.work_next = &a.tc->fb_next;
-            f.nmax = P.fb_tri ? P.tc_nmax : c.max_points;
+            f.nmax = P.nmax_smem;
             f.percol_max = default_percol_max(8);
             f.panel = 16;
-            CK(launch_solve(kind, P.fb_tri, 512, f, P.fb_grid, P.fb_smem, s));
+            CK(launch_solve(kind, true, P.fb_nthr, f, P.fb_grid, P.fb_smem, s));
             ++h->last_launches;
+            if (P.tc_nmax > P.nmax_smem) {  // and those beyond the shared-memory kernels
+                f.work = a.tc_fb + nvox;
+                f.work_count = &a.tc->fb2_count;
+                f.work_next = &a.tc->fb2_next;
+                if (x.d_tall && !a.pvar) {
+                    CK(launch_tall(kind, f, x.d_tall, h->tall_stride, (P.tc_nmax + 31) / 32 * 32,
+                                   h->sms, s));
+                } else {
+                    f.nmax = c.max_points;
+                    CK(launch_solve(kind, false, 512, f, P.fbb_grid, P.fbb_smem, s));
+                }
+                ++h->last_launches;
+            }
         }
         if (a.pos) {
             CK(launch_init_tc(a, h->sms, s));

@@ -33,6 +33,7 @@ struct TcCounters {
     unsigned long long total, used;
     int32_t count, next;
     int32_t fb_count, fb_next;  // voxels the tensor-core solve variant could not hand over
+    int32_t fb2_count, fb2_next;  // the same, too large for the shared-memory kernels
 };
 
 struct SolveArgs {
@@ -86,7 +87,9 @@ struct SolveArgs {
     TcCounters* tc;
     int32_t* tc_v;       // voxels queued for k_var_tc (one entry per voxel at most)
     int64_t* tc_off;     // their byte offsets in tc_ws
-    int32_t* tc_fb;      // voxels re-solved by the regular kernel (workspace full)
+    int32_t* tc_fb;      // voxels re-solved by the regular kernel (workspace full): n <=
+                         // fb_nsmall at [0, nvox), larger ones at [nvox, 2 nvox)
+    int fb_nsmall;       // largest n of the shared-memory re-solve
     long long* tc_off_v; // per output row: workspace byte offset, -1 if not handed over
     int tc_nmax;         // largest n that takes the tensor-core variance (factor in shared memory)
     int tc_nmax_gl;      // the same for voxels whose factor lives in the global workspace

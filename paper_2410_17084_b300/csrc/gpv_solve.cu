@@ -593,6 +593,16 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     const int64_t beg = A.offsets[v];
     const int n = (int)(A.offsets[v + 1] - beg);
     const int G = A.G, Gp = A.Gp, GG = G * G;
+    if (TCV && A.tc->total > A.tc_cap) {
+        // the call's voxels need more workspace than it has: the regular kernels solve
+        // them all (decided once per call after the classification, so it does not depend
+        // on scheduling); nothing is factored here
+        if (tid == 0) {
+            const bool big = n > A.fb_nsmall;
+            A.tc_fb[(big ? (int64_t)A.nvox : 0) + atomicAdd(big ? &A.tc->fb2_count : &A.tc->fb_count, 1)] = v;
+        }
+        return;
+    }
 
     float* pts = reinterpret_cast<float*>(smem + P.off_pts);
     T* x1 = reinterpret_cast<T*>(smem + P.off_vec);
@@ -779,7 +789,10 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
     }
     __syncthreads();
     if (TCV && !tc) {  // workspace full: the regular kernel re-solves this voxel
-        if (tid == 0) A.tc_fb[atomicAdd(&A.tc->fb_count, 1)] = v;
+        if (tid == 0) {
+            const bool big = n > A.fb_nsmall;
+            A.tc_fb[(big ? (int64_t)A.nvox : 0) + atomicAdd(big ? &A.tc->fb2_count : &A.tc->fb_count, 1)] = v;
+        }
         __syncthreads();
         return;
     }

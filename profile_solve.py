@@ -31,10 +31,11 @@ def main():
                     choices=["quadric", "mixed", "stress", "plane", "serving"])
     ap.add_argument("--scans", type=int, default=12)
     ap.add_argument("--path", default="solve", choices=["solve", "alg3", "lp", "raster"])
+    ap.add_argument("--tc-mb", type=int, default=4096, help="tensor-core variance workspace")
     a = ap.parse_args()
     build.build()
     if a.workload == "serving":  # scans one after another through the serving path
-        from . import serve
+        from paper_2410_17084_b300 import serve
         scene = synth.lidar_scene()
         scans = [synth.lidar_scan(scene, k) for k in range(a.scans)]
         srv = serve.Server(serve.serving_config())
@@ -48,7 +49,8 @@ def main():
     d = gv.batch_to_device(b)
     g = gv.GpVoxels(gv.gp_voxels_config_default(
         voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau,
-        max_points=int(max(256, b.counts.max())), max_voxels=b.nvox, precision=a.precision))
+        max_points=int(max(256, b.counts.max())), max_voxels=b.nvox, precision=a.precision,
+        tc_workspace_mb=a.tc_mb))
     out = g.outputs(b.nvox, "cuda", init=bool(a.init) or a.path in ("lp", "raster"))
     if a.path != "solve":
         _other_path(a, b, d, g, out)
