@@ -77,11 +77,12 @@ template <int NSL> struct Plan {
 constexpr int kLs = kBP + 1;  // row stride of the diagonal-block buffers (bank spread)
 
 // dynamic shared memory: [stages][x1, x2: np each][Lkk, D: 32 x 33 each][rd, zp: 32]
+// [T: 16 x 16, the products of the blocked inverse]
 __host__ __device__ inline int tall_smem_bytes(int nsl, int npmax, int tsize)
 {
     int o = kNSt * nsl * (kSlA + kSlB);
     o += 2 * npmax * tsize;
-    o += (2 * kBP * kLs + 2 * kBP) * tsize;
+    o += (2 * kBP * kLs + 2 * kBP + 256) * tsize;
     return (o + 15) & ~15;
 }
 
@@ -223,6 +224,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
     T* Dm = Lkk + kBP * kLs;   // its inverse (lower triangle, zeros above)
     T* rd = Dm + kBP * kLs;    // 1 / L_jj
     T* zp = rd + kBP;          // z of the panel
+    T* Tb = zp + kBP;          // 16 x 16 products of the blocked inverse
 
     if (threadIdx.x < G)
         nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
@@ -489,69 +491,96 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         }
                     }
                     const bool diag = t == 0 && qd == 0;  // warp 4: the rows of the diagonal block
-                    if (diag) {
-                        // ---- factor the diagonal block, invert it, z of the panel ------------
+                    if (t == 0) {
+                        // ---- group A (128 threads): factor the diagonal block, invert it, z of
+                        // the panel; warp 4 holds its rows -------------------------------------
+                        if (diag) {
 #pragma unroll
-                        for (int j = 0; j < kBP; ++j) Lkk[lane * kLs + j] = row[j];
-                        __syncwarp();
+                            for (int j = 0; j < kBP; ++j) Lkk[lane * kLs + j] = row[j];
+                            zp[lane] = yv[c0 + lane] - rs[2 * (c0 + lane)];
+                        }
+                        named_sync(1, 128);
                         float dmn = 3.0e38f, dmx = 0.f;
                         int bad = 0;
+                        const int ui = ri >> 2, uq = ri & 3;  // update task: row ui, columns = uq mod 4
                         for (int k = 0; k < kBP; ++k) {  // right-looking, one column per step
-                            __syncwarp();
                             const T d = Lkk[k * kLs + k];
-                            const float dh = hi_of(d);
-                            if (c0 + k < n) {
+                            if (ri == 0 && c0 + k < n) {
+                                const float dh = hi_of(d);
                                 if (!(dh > 0.f)) bad = 1;
                                 dmn = fminf(dmn, dh);
                                 dmx = fmaxf(dmx, dh);
                             }
-                            const T ls = gsqrt(d), il = grcp(ls);
-                            __syncwarp();
-                            if (lane == k) { Lkk[k * kLs + k] = ls; rd[k] = il; }
-                            if (lane > k) Lkk[lane * kLs + k] = Lkk[lane * kLs + k] * il;
-                            __syncwarp();
-                            if (lane > k) {
-                                const T lik = Lkk[lane * kLs + k];
-                                for (int mm = k + 1; mm <= lane; ++mm)
-                                    Lkk[lane * kLs + mm] = gfnma(lik, Lkk[mm * kLs + k], Lkk[lane * kLs + mm]);
+                            const T il = grsqrt(d);  // 1 / L_kk
+                            if (ri > k && ri < kBP) Lkk[ri * kLs + k] = Lkk[ri * kLs + k] * il;
+                            named_sync(1, 128);
+                            if (ri == k) { Lkk[k * kLs + k] = d * il; rd[k] = il; }
+                            if (ui > k) {
+                                const T lik = Lkk[ui * kLs + k];
+                                const int m0 = k + 1 + ((uq - k - 1) & 3);
+#pragma unroll
+                                for (int s8 = 0; s8 < 8; ++s8) {
+                                    const int mm = m0 + 4 * s8;
+                                    if (mm <= ui)
+                                        Lkk[ui * kLs + mm] = gfnma(lik, Lkk[mm * kLs + k], Lkk[ui * kLs + mm]);
+                                }
+                            }
+                            named_sync(1, 128);
+                        }
+                        // D = L_pp^-1 by blocks: the eight 4 x 4 diagonal blocks directly, then
+                        // three levels D21 = -D22 (L21 D11) doubling the block size; zeros above
+                        for (int e = ri; e < kBP * kBP; e += 128) {
+                            const int i = e >> 5, j = e & 31;
+                            if (j > i || (i >> 2) != (j >> 2)) Dm[i * kLs + j] = zero<T>();
+                        }
+                        if (ri < 8) {
+                            const int o = 4 * ri;
+                            for (int j = 0; j < 4; ++j) {
+                                Dm[(o + j) * kLs + o + j] = rd[o + j];
+                                for (int i = j + 1; i < 4; ++i) {
+                                    T acc = zero<T>();
+                                    for (int k = j; k < i; ++k)
+                                        acc_fma(acc, Lkk[(o + i) * kLs + o + k], Dm[(o + k) * kLs + o + j]);
+                                    Dm[(o + i) * kLs + o + j] = -(acc_norm(acc) * rd[o + i]);
+                                }
                             }
                         }
-                        __syncwarp();
-                        // D = L_pp^-1, lane j forms column j
-                        for (int i = 0; i < kBP; ++i) Dm[i * kLs + lane] = zero<T>();
-                        __syncwarp();
-                        Dm[lane * kLs + lane] = rd[lane];
-                        for (int i = lane + 1; i < kBP; ++i) {
-                            T acc = zero<T>();
-                            for (int k = lane; k < i; ++k) acc_fma(acc, Lkk[i * kLs + k], Dm[k * kLs + lane]);
-                            Dm[i * kLs + lane] = -(acc_norm(acc) * rd[i]);
+                        named_sync(1, 128);
+                        for (int h = 4; h < kBP; h *= 2) {
+                            const int E = (kBP / (2 * h)) * h * h;
+                            for (int e = ri; e < E; e += 128) {  // T = L21 D11
+                                const int bb = e / (h * h), i = (e / h) % h, j = e % h, o = 2 * h * bb;
+                                T acc = zero<T>();
+                                for (int k = j; k < h; ++k)
+                                    acc_fma(acc, Lkk[(o + h + i) * kLs + o + k], Dm[(o + k) * kLs + o + j]);
+                                Tb[e] = acc_norm(acc);
+                            }
+                            named_sync(1, 128);
+                            for (int e = ri; e < E; e += 128) {  // D21 = -D22 T
+                                const int bb = e / (h * h), i = (e / h) % h, j = e % h, o = 2 * h * bb;
+                                T acc = zero<T>();
+                                for (int k = 0; k <= i; ++k)
+                                    acc_fma(acc, Dm[(o + h + i) * kLs + o + h + k], Tb[bb * h * h + k * h + j]);
+                                Dm[(o + h + i) * kLs + o + j] = -acc_norm(acc);
+                            }
+                            named_sync(1, 128);
                         }
-                        __syncwarp();
                         // z_p = D (y_p - w_p)
-                        {
-                            zp[lane] = yv[c0 + lane] - rs[2 * (c0 + lane)];
-                            __syncwarp();
-                            T zl = zero<T>();
-                            for (int k = 0; k <= lane; ++k) acc_fma(zl, Dm[lane * kLs + k], zp[k]);
-                            __syncwarp();
-                            zp[lane] = acc_norm(zl);
-                        }
-                        if (bad) sh.fail = 1;
-                        for (int o = 16; o > 0; o >>= 1) {
-                            dmn = fminf(dmn, __shfl_xor_sync(0xffffffffu, dmn, o));
-                            dmx = fmaxf(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
-                        }
-                        if (lane == 0) {
+                        T zl = zero<T>();
+                        if (ri < kBP)
+                            for (int k = 0; k <= ri; ++k) acc_fma(zl, Dm[ri * kLs + k], zp[k]);
+                        named_sync(1, 128);
+                        if (ri < kBP) zp[ri] = acc_norm(zl);
+                        if (ri == 0) {
+                            if (bad) sh.fail = 1;
                             sh.dmin = fminf(sh.dmin, dmn);
                             sh.dmax = fmaxf(sh.dmax, dmx);
                         }
                         __threadfence_block();
-                        __syncwarp();
-                        named_arrive(1, 128);                 // warps 5..7
-                        if (T_ > 1) named_arrive(2, 160);     // the odd tiles' group
-                    } else {
-                        if (t == 0) named_sync(1, 128);
-                        else if (t == 1) named_sync(2, 160);
+                        named_sync(1, 128);
+                        if (diag && T_ > 1) named_arrive(2, 160);  // the odd tiles' group may go on
+                    } else if (t == 1) {
+                        named_sync(2, 160);
                     }
                     // ---- L[r, panel] = P[r, :] D^T (the diagonal rows take L_pp itself), the
                     // running sums, the slices: two columns per step ------------------------
