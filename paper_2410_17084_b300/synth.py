@@ -177,6 +177,18 @@ def stress_batch(nvox: int = 1000000, seed: int = 4, axes: str = "random") -> Vo
                      ell=ell, sd=sd)
 
 
+def fixed_batch(nvox: int, n: int, G: int = 9, seed: int = 5) -> VoxelBatch:
+    """nvox voxels of exactly n points each, otherwise as the stress workload (quadric
+    surfaces, lengthscale U[0.1, 0.4], noise sd U[0.01, 0.05]); for per-size timing."""
+    rng = np.random.default_rng(seed)
+    counts = np.full(nvox, n, dtype=np.int64)
+    ell = rng.uniform(0.1, 0.4, nvox)
+    sd = rng.uniform(0.01, 0.05, nvox)
+    ns = 3 if G % 3 == 0 else (4 if G % 4 == 0 else 1)
+    return _assemble(f"fixed{n}", rng, counts, 0.5, G, ns, G // ns, 4, _quadric, axes="random",
+                     ell=ell, sd=sd)
+
+
 def point_noise(b: VoxelBatch, seed: int, lo: float = 0.1, hi: float = 10.0) -> np.ndarray:
     """Per-point noise variances for a batch: each point's voxel sn2 times a log-uniform
     factor on [lo, hi] (the spread of fed-back variances around the sensor's)."""

@@ -1,6 +1,7 @@
 """Run one batched solve on a prefix of a synthetic workload, for profilers (ncu).
 
     python profile_solve.py --nvox 10000 --precision 1
+    python profile_solve.py --workload fixed --n 512 --nvox 296
 
 prints the CUDA-event time of each repetition.  Workloads: quadric (the bench workload),
 mixed (escalation workload), stress (1M-voxel workload), plane; with --path alg3 the
@@ -28,10 +29,12 @@ def main():
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--init", type=int, default=1)
     ap.add_argument("--workload", default="quadric",
-                    choices=["quadric", "mixed", "stress", "plane", "serving"])
+                    choices=["quadric", "mixed", "stress", "plane", "serving", "fixed"])
+    ap.add_argument("--n", type=int, default=512, help="points per voxel of the fixed workload")
     ap.add_argument("--scans", type=int, default=12)
     ap.add_argument("--path", default="solve", choices=["solve", "alg3", "lp", "raster"])
     ap.add_argument("--tc-mb", type=int, default=4096, help="tensor-core variance workspace")
+    ap.add_argument("--tall-min", type=int, default=0, help="tall-matrix path above this n")
     a = ap.parse_args()
     build.build()
     if a.workload == "serving":  # scans one after another through the serving path
@@ -43,14 +46,17 @@ def main():
         srv.close()
         print("per-scan ms", [round(x * 1e3, 1) for x in lat.tolist()])
         return
-    gen = {"quadric": synth.quadric_batch, "mixed": synth.mixed_batch,
-           "stress": synth.stress_batch, "plane": synth.plane_batch}[a.workload]
-    b = gen(a.nvox)
+    if a.workload == "fixed":
+        b = synth.fixed_batch(a.nvox, a.n)
+    else:
+        gen = {"quadric": synth.quadric_batch, "mixed": synth.mixed_batch,
+               "stress": synth.stress_batch, "plane": synth.plane_batch}[a.workload]
+        b = gen(a.nvox)
     d = gv.batch_to_device(b)
     g = gv.GpVoxels(gv.gp_voxels_config_default(
         voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau,
         max_points=int(max(256, b.counts.max())), max_voxels=b.nvox, precision=a.precision,
-        tc_workspace_mb=a.tc_mb))
+        tc_workspace_mb=a.tc_mb, tall_min_points=a.tall_min))
     out = g.outputs(b.nvox, "cuda", init=bool(a.init) or a.path in ("lp", "raster"))
     if a.path != "solve":
         _other_path(a, b, d, g, out)
