@@ -18,7 +18,7 @@ SOURCES = ["gpv_api.cu", "gpv_solve.cu", "gpv_store.cu", "gpv_noalloc.cu", "gpv_
            "gpv_lp.cu", "gpv_raster.cu", "gpv_peak.cu", "gpv_vartc.cu", "gpv_tall.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
-         "-fvisibility=hidden", "--expt-relaxed-constexpr", "--split-compile=4"]
+         "-fvisibility=hidden", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:
