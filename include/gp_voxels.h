@@ -216,13 +216,16 @@ GPV_API int gp_voxels_solve_csr_noise(gp_voxels_t* h, const float* d_xyz,
  * Inputs as gp_voxels_solve_csr.  Outputs (device, caller-owned):
  *   d_axis [nvox] u8, d_mean [nvox, G*G], d_status [nvox] (GPV_VOX_* bits),
  *   d_cov [nvox, G*G, G*G] FP32 row-major: Sigma*(q, q') at d_cov[(v G^2 + q) G^2 + q'].
- * Voxels below tau, above the size this path holds in one CTA's shared memory (*h_nmax,
- * about 200 points at G = 16) or whose FP32 LU meets a zero pivot (GPV_VOX_NOT_SPD) get
- * mean 0 and the prior K**.  FP32 LU and inverse lose about log10(cond(ky)) digits:
- * on dense voxels the variances are far less accurate than gp_voxels_solve_csr's.
- * The first call allocates a workspace of about 512 MB (counted against mem_budget) and
- * synchronises nothing; later calls allocate nothing.  h_nmax (may be NULL) receives the
- * largest n solved.  Errors: GPV_EINVAL, GPV_EBUDGET, GPV_ENOMEM, GPV_ECUDA. */
+ * Every voxel up to max_points is solved: ky lives in one CTA's shared memory up to about
+ * 200 points at G = 16, in a global-memory slice per CTA above (one persistent launch per
+ * chunk for those).  Voxels below tau, above max_points (GPV_VOX_TOO_LARGE) or whose FP32 LU
+ * meets a zero pivot (GPV_VOX_NOT_SPD) get mean 0 and the prior K**.  FP32 LU and inverse
+ * lose about log10(cond(ky)) digits: on dense voxels the variances are far less accurate
+ * than gp_voxels_solve_csr's.  The first call allocates a workspace of about 512 MB plus,
+ * when max_points exceeds the shared-memory size, one kp x kp FP32 matrix per SM
+ * (kp = max_points rounded up to 32; 600 MB at 1024 points), counted against mem_budget;
+ * later calls allocate nothing.  h_nmax (may be NULL) receives the largest n solved
+ * (max_points).  Errors: GPV_EINVAL, GPV_EBUDGET, GPV_ENOMEM, GPV_ECUDA. */
 GPV_API int gp_voxels_solve_alg3(gp_voxels_t* h, const float* d_xyz, const int64_t* d_offsets,
                                  int32_t nvox, const float* d_centres, const float* d_lambda,
                                  const float* d_sf2, const float* d_sn2, uint8_t* d_axis,

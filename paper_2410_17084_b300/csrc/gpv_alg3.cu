@@ -35,7 +35,8 @@ struct A3Plan {
     int off_pts, off_x1, off_x2, off_f, off_fa, off_fb, off_tmp, off_piv, off_src, off_A, total;
 };
 
-__host__ __device__ inline A3Plan a3_plan(int nmax, int G)
+// big: ky and the K* factors live in global memory (voxels beyond shared memory)
+__host__ __device__ inline A3Plan a3_plan(int nmax, int G, bool big = false)
 {
     A3Plan p;
     int o = 0;
@@ -44,12 +45,12 @@ __host__ __device__ inline A3Plan a3_plan(int nmax, int G)
     p.off_x1 = take(4 * nmax);
     p.off_x2 = take(4 * nmax);
     p.off_f = take(4 * nmax);
-    p.off_fa = take(4 * nmax * G);
-    p.off_fb = take(4 * nmax * G);
+    p.off_fa = take(big ? 0 : 4 * nmax * G);
+    p.off_fb = take(big ? 0 : 4 * nmax * G);
     p.off_tmp = take(4 * nmax);
     p.off_piv = take(4 * nmax);
     p.off_src = take(4 * nmax);
-    p.off_A = take(4 * nmax * nmax);
+    p.off_A = take(big ? 0 : 4 * nmax * nmax);
     p.total = o;
     return p;
 }
@@ -59,14 +60,13 @@ __device__ __forceinline__ float node_pos(int i, int G, float s)
     return (float)(-0.5 * (double)s + ((double)i + 0.5) * (double)s / (double)G);
 }
 
-__global__ void __launch_bounds__(kA3Threads) k_alg3_factor(Alg3Args a)
+// One voxel of kernel A.  BIG: ky (row-major, stride n) and the K* factors in global
+// memory (this CTA's slice of ws_A, the slot's workspace factors), the rest in shared.
+template <bool BIG>
+__device__ void alg3_factor_one(const Alg3Args& a, int slot, unsigned char* sm, float* red,
+                                int& s_axis, int& s_fail, int& s_p, float* s_pv, int* s_pi)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ float red[6 * 32];
-    __shared__ int s_axis, s_fail, s_p;
-    __shared__ float s_pv[32];
-    __shared__ int s_pi[32];
-    const int slot = blockIdx.x, v = a.v0 + slot;
+    const int v = a.v0 + slot;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int G = a.G, Q = G * G;
     const int64_t beg = a.offsets[v];
@@ -85,17 +85,21 @@ __global__ void __launch_bounds__(kA3Threads) k_alg3_factor(Alg3Args a)
         }
         return;
     }
-    const A3Plan P = a3_plan(a.nhi, G);
+    const A3Plan P = a3_plan(a.nhi, G, BIG);
+    const int Kp = a.kp;
     float* pts = reinterpret_cast<float*>(sm + P.off_pts);
     float* x1 = reinterpret_cast<float*>(sm + P.off_x1);
     float* x2 = reinterpret_cast<float*>(sm + P.off_x2);
     float* fv = reinterpret_cast<float*>(sm + P.off_f);
-    float* fa = reinterpret_cast<float*>(sm + P.off_fa);
-    float* fb = reinterpret_cast<float*>(sm + P.off_fb);
+    float* FA = a.ws_fa + (int64_t)slot * Kp * G;  // the K* factors for kernel B
+    float* FB = a.ws_fb + (int64_t)slot * Kp * G;
+    float* fa = BIG ? FA : reinterpret_cast<float*>(sm + P.off_fa);
+    float* fb = BIG ? FB : reinterpret_cast<float*>(sm + P.off_fb);
     float* tmp = reinterpret_cast<float*>(sm + P.off_tmp);
     int* piv = reinterpret_cast<int*>(sm + P.off_piv);
     int* src = reinterpret_cast<int*>(sm + P.off_src);
-    float* A = reinterpret_cast<float*>(sm + P.off_A);  // row-major, stride n
+    float* A = BIG ? a.ws_A + (int64_t)blockIdx.x * Kp * Kp   // row-major, stride n
+                   : reinterpret_cast<float*>(sm + P.off_A);
 
     for (int t = tid; t < 3 * n; t += blockDim.x) pts[t] = __ldg(a.xyz + 3 * beg + t);
     __syncthreads();
@@ -243,7 +247,6 @@ __global__ void __launch_bounds__(kA3Threads) k_alg3_factor(Alg3Args a)
     __syncthreads();
 
     // ---- k_k* = K*^T ky^-1 (G^2 x n), written as a TF32 split pair ------------------
-    const int Kp = a.kp;
     float* Pb = a.ws_pb + (int64_t)slot * Q * Kp;
     float* Ps = a.ws_ps + (int64_t)slot * Q * Kp;
     {  // 4 queries x 4 columns per thread, 16 accumulators
@@ -285,10 +288,9 @@ __global__ void __launch_bounds__(kA3Threads) k_alg3_factor(Alg3Args a)
                 }
         }
     }
-    // factors of K* for kernel B
-    float* FA = a.ws_fa + (int64_t)slot * Kp * G;
-    float* FB = a.ws_fb + (int64_t)slot * Kp * G;
-    for (int t = tid; t < n * G; t += blockDim.x) { FA[t] = fa[t]; FB[t] = fb[t]; }
+    // factors of K* for kernel B (already in place for BIG)
+    if (!BIG)
+        for (int t = tid; t < n * G; t += blockDim.x) { FA[t] = fa[t]; FB[t] = fb[t]; }
     __syncthreads();
     // ---- mu* = m + k_k* (f - m) ---------------------------------------------------------
     for (int q = tid; q < Q; q += blockDim.x) {
@@ -302,6 +304,30 @@ __global__ void __launch_bounds__(kA3Threads) k_alg3_factor(Alg3Args a)
         a.status[v] = VOX_OK;
         a.ws_status[slot] = VOX_OK;
         a.ws_n[slot] = n;
+    }
+}
+
+__global__ void __launch_bounds__(kA3Threads) k_alg3_factor(Alg3Args a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ float red[6 * 32];
+    __shared__ int s_axis, s_fail, s_p;
+    __shared__ float s_pv[32];
+    __shared__ int s_pi[32];
+    alg3_factor_one<false>(a, blockIdx.x, sm, red, s_axis, s_fail, s_p, s_pv, s_pi);
+}
+
+// voxels beyond shared memory: persistent CTAs over the chunk's slots, ky in global memory
+__global__ void __launch_bounds__(kA3Threads) k_alg3_factor_big(Alg3Args a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ float red[6 * 32];
+    __shared__ int s_axis, s_fail, s_p;
+    __shared__ float s_pv[32];
+    __shared__ int s_pi[32];
+    for (int slot = blockIdx.x; slot < a.nchunk; slot += gridDim.x) {
+        alg3_factor_one<true>(a, slot, sm, red, s_axis, s_fail, s_p, s_pv, s_pi);
+        __syncthreads();
     }
 }
 
@@ -444,17 +470,25 @@ int alg3_max_n(int G)
     return best;
 }
 
+int alg3_big_ctas()
+{
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
 cudaError_t alg3_launch_chunk(const Alg3Args& a0, int nchunk, cudaStream_t s, int* nlaunch)
 {
     *nlaunch = 0;
     // kernel A in three size classes, each launch with the shared memory of its largest n
-    const int cls[3] = {64, 128, a0.nmax};
+    const int nsm = a0.nsm < a0.nmax ? a0.nsm : a0.nmax;  // largest n of the shared-memory classes
+    const int cls[3] = {64, 128, nsm};
     cudaError_t e = cudaFuncSetAttribute(k_alg3_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         a3_plan(a0.nmax, a0.G).total);
+                                         a3_plan(nsm, a0.G).total);
     if (e != cudaSuccess) return e;
     int lo = 0;
     for (int c = 0; c < 3; ++c) {
-        const int hi = c < 2 ? (cls[c] < a0.nmax ? cls[c] : a0.nmax) : a0.nmax;
+        const int hi = c < 2 ? (cls[c] < nsm ? cls[c] : nsm) : nsm;
         if (hi <= lo && c > 0) continue;
         Alg3Args a = a0;
         a.nlo = lo;
@@ -464,6 +498,19 @@ cudaError_t alg3_launch_chunk(const Alg3Args& a0, int nchunk, cudaStream_t s, in
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         ++*nlaunch;
         lo = hi;
+    }
+    if (a0.nmax > a0.nsm) {  // voxels beyond shared memory
+        Alg3Args a = a0;
+        a.nlo = a0.nsm;
+        a.nhi = a0.nmax;
+        a.nchunk = nchunk;
+        const int smemA = a3_plan(a0.nmax, a0.G, true).total;
+        e = cudaFuncSetAttribute(k_alg3_factor_big, cudaFuncAttributeMaxDynamicSharedMemorySize, smemA);
+        if (e != cudaSuccess) return e;
+        const int grid = nchunk < alg3_big_ctas() ? nchunk : alg3_big_ctas();
+        k_alg3_factor_big<<<grid, kA3Threads, smemA, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*nlaunch;
     }
     const Alg3Args& a = a0;
     const int Q = a.G * a.G;

@@ -120,8 +120,8 @@ struct gp_voxels {
     int last_launches = 0;          // kernels queued by the last solve call
     // workspace of the Alg. 3 formulation (allocated by its first call)
     struct {
-        int nmax = 0, kp = 0, chunk = 0;
-        float *pb = nullptr, *ps = nullptr, *fa = nullptr, *fb = nullptr;
+        int nmax = 0, nsm = 0, kp = 0, chunk = 0;
+        float *pb = nullptr, *ps = nullptr, *fa = nullptr, *fb = nullptr, *A = nullptr;
         uint32_t* st = nullptr;
         int32_t* n = nullptr;
     } a3;
@@ -441,7 +441,7 @@ static void release(gp_voxels_t* h)
     cudaFree(h->d_one); cudaFree(h->d_ident); cudaFree(h->d_pl_next);
     for (auto& e : h->ev_tall)
         if (e) cudaEventDestroy(e);
-    cudaFree(h->a3.pb); cudaFree(h->a3.ps); cudaFree(h->a3.fa); cudaFree(h->a3.fb);
+    cudaFree(h->a3.pb); cudaFree(h->a3.ps); cudaFree(h->a3.fa); cudaFree(h->a3.fb); cudaFree(h->a3.A);
     cudaFree(h->a3.st); cudaFree(h->a3.n);
     cudaFree(h->lp.keys); cudaFree(h->lp.head); cudaFree(h->lp.next); cudaFree(h->lp.pending);
     cudaFree(h->lp.counters); cudaFree(h->lp.arg); cudaFree(h->lp.best); cudaFree(h->lp.smax);
@@ -867,12 +867,16 @@ static int alg3_workspace(gp_voxels_t* h)
     if (h->a3.pb) return GPV_OK;
     const gp_voxels_config& c = h->cfg;
     const int G = c.grid_side, Q = G * G;
-    const int nmax = std::min(c.max_points, alg3_max_n(G));
+    // every voxel up to max_points: ky in shared memory up to nsm points, in a global slice
+    // per CTA of the persistent class above
+    const int nsm = std::min(c.max_points, alg3_max_n(G));
+    const int nmax = c.max_points;
     if (nmax < c.tau) return GPV_EINVAL;
     const int kp = (nmax + 31) / 32 * 32;
     const size_t per = (size_t)2 * Q * kp * 4 + (size_t)2 * kp * G * 4 + 8;
     int chunk = (int)std::min<size_t>((size_t)c.max_voxels, std::max<size_t>(1, ((size_t)512 << 20) / per));
-    const size_t need = per * (size_t)chunk;
+    const size_t bigA = nmax > nsm ? (size_t)alg3_big_ctas() * kp * kp * 4 : 0;
+    const size_t need = per * (size_t)chunk + bigA;
     if (c.mem_budget && h->bytes + need > c.mem_budget) return GPV_EBUDGET;
     auto al = [&](void** p, size_t b) -> int {
         cudaError_t e = cudaMalloc(p, b);
@@ -888,7 +892,9 @@ static int alg3_workspace(gp_voxels_t* h)
     if ((rc = al((void**)&h->a3.fb, (size_t)chunk * kp * G * 4)) != GPV_OK) return rc;
     if ((rc = al((void**)&h->a3.st, (size_t)chunk * 4)) != GPV_OK) return rc;
     if ((rc = al((void**)&h->a3.n, (size_t)chunk * 4)) != GPV_OK) return rc;
+    if (bigA && (rc = al((void**)&h->a3.A, bigA)) != GPV_OK) return rc;
     h->a3.nmax = nmax;
+    h->a3.nsm = nsm;
     h->a3.kp = kp;
     h->a3.chunk = chunk;
     return GPV_OK;
@@ -914,7 +920,7 @@ extern "C" int gp_voxels_solve_alg3(gp_voxels_t* h, const float* d_xyz, const in
     a.xyz = d_xyz; a.offsets = d_offsets; a.centres = d_centres;
     a.lam = d_lambda; a.sf2 = d_sf2; a.sn2 = d_sn2;
     a.size = c.voxel_size; a.G = c.grid_side; a.tau = c.tau; a.mean_mode = c.mean_mode;
-    a.nmax = h->a3.nmax; a.kp = h->a3.kp;
+    a.nmax = h->a3.nmax; a.nsm = h->a3.nsm; a.kp = h->a3.kp; a.ws_A = h->a3.A;
     a.axis = d_axis; a.mean = d_mean; a.cov = d_cov; a.status = d_status;
     a.ws_pb = h->a3.pb; a.ws_ps = h->a3.ps; a.ws_fa = h->a3.fa; a.ws_fb = h->a3.fb;
     a.ws_status = h->a3.st; a.ws_n = h->a3.n;

@@ -84,7 +84,7 @@ def test_tensor_core_workspace_split_between_contexts(libpath):
         off = g.gp_voxels_query_sizes(serve.serving_config(mem_budget=0, scan_slots=slots,
                                                            tc_workspace_mb=0))
         on = g.gp_voxels_query_sizes(serve.serving_config(mem_budget=0, scan_slots=slots))
-        lists = ((1 << 16) + slots * (1 << 15)) * 24 + (slots + 1) * 4096
+        lists = ((1 << 16) + slots * (1 << 15)) * 28 + (slots + 1) * 4096
         assert 4095 * mb < on - off <= 4096 * mb + lists
     budgeted = serve.serving_config()
     assert g.gp_voxels_query_sizes(budgeted) <= budgeted.mem_budget
@@ -94,4 +94,4 @@ def test_tensor_core_workspace_split_between_contexts(libpath):
     fb = dict(mem_budget=0, eta=0.3, noise_floor=4e-6)
     on = g.gp_voxels_query_sizes(serve.serving_config(**fb))
     off = g.gp_voxels_query_sizes(serve.serving_config(tc_workspace_mb=0, **fb))
-    assert 4095 * mb < on - off <= 4096 * mb + (1 << 16) * 24 + 4096
+    assert 4095 * mb < on - off <= 4096 * mb + (1 << 16) * 28 + 4096
