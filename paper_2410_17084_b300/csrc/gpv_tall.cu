@@ -32,6 +32,9 @@
 // over the row norms, level 0 stays below 2^14 grid units and level 1 below 2^20 for any
 // K; the levels of remainder slices (products of up to 2^14 units, signs close to
 // random) grow like sqrt(K) 2^14 / 3 (2^17.4 at K = 1024, against 2^24 for exactness).
+// With six slices levels 4 and 5 share one accumulator: level 5 then rounds to the FP32
+// grid of the level-4 sum, an error below 2^-45 of |L_r| |L_c| even when every rounding
+// has the same sign, where the float-float working type holds about 2^-44.
 // The mixed path uses NSL = 6 (48 bits, 21 products per element); the FP32 path NSL = 4
 // (32 bits, 10 products: the fixed-point grid of a row then resolves entries well below
 // the row's norm to about FP32's own precision).  Pairs with s + t >= NSL are dropped (below 2^-8 NSL of the row
@@ -43,7 +46,10 @@
 // slice, one 32 x 32 tile of each B slice, contiguous in the slice store) with
 // cp.async.bulk into a ring of shared-memory stages, each completing on an mbarrier;
 // one thread of warp 1 issues the MMAs (M = 128, N = 32, K = 16, kind::f16) of a tile
-// into one of two accumulator sets (NSL levels x 32 columns each) and commits; warps
+// into one of three accumulator sets (one 32-column accumulator per level) and commits:
+// tile 0 of a panel, whose diagonal block every other row waits for, has all but its last
+// chunk accumulated in set 2 during the previous panel, the other tiles alternate between
+// sets 0 and 1; warps
 // 4..7 and 8..11 take the even and odd tiles: they read the levels with tcgen05.ld (lane
 // = row), form P in the working type, solve, cut and store the slices.  Every wait is
 // bounded; a wait that gives up marks the voxel GPV_VOX_FAILED and the CTA stops.
@@ -70,8 +76,12 @@ constexpr int kGrpBytes = 512;       // one 8-row group of a 32-column panel sli
 
 template <int NSL> struct Plan {
     static constexpr int stage = NSL * (kSlA + kSlB);
-    static constexpr int set_cols = NSL * kBP;  // tensor-memory columns of one set
-    static constexpr int tmem_cols = 2 * set_cols <= 256 ? 256 : 512;
+    // accumulators per set: one per level, except that with six slices levels 4 and 5
+    // share the last one
+    static constexpr int nlv = NSL == 6 ? 5 : NSL;
+    static constexpr int set_cols = nlv * kBP;  // tensor-memory columns of one set
+    static constexpr int tmem_cols = 512;       // three sets
+    static_assert(3 * set_cols <= tmem_cols, "tensor memory");
 };
 
 constexpr int kLs = kBP + 1;  // row stride of the diagonal-block buffers (bank spread)
@@ -172,7 +182,7 @@ __device__ __forceinline__ int64_t sl_off(int p, int s, int g, int nsl, int RG)
 }
 
 struct Sh {  // static shared state
-    uint64_t full[kNSt], empty[kNSt], acc_full[2], acc_empty[2];
+    uint64_t full[kNSt], empty[kNSt], acc_full[3], acc_empty[3];
     uint32_t tmem;
     int v, abort, broken, fail;
     float dmin, dmax;
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
         }
     if (tid == 0) {
         for (int i = 0; i < kNSt; ++i) { umma::mbar_init(&sh.full[i], 1); umma::mbar_init(&sh.empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { umma::mbar_init(&sh.acc_full[i], 1); umma::mbar_init(&sh.acc_empty[i], 4); }
+        for (int i = 0; i < 3; ++i) { umma::mbar_init(&sh.acc_full[i], 1); umma::mbar_init(&sh.acc_empty[i], 4); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh.broken = 0;
     }
@@ -248,8 +258,8 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
     const uint32_t tmem = sh.tmem;
 
     // pipeline counters (each role keeps its own copy of the common schedule)
-    uint32_t cnt = 0;            // operand chunks (producer, MMA issuer)
-    uint32_t use[2] = {0, 0};    // tiles per accumulator set (MMA issuer, epilogue groups)
+    uint32_t cnt = 0;               // operand chunks (producer, MMA issuer)
+    uint32_t use[3] = {0, 0, 0};    // completed tiles per accumulator set (MMA issuer, epilogue)
     const uint32_t idesc = umma::idesc_bf16(kMT, kBP);
 
     const int total = *A.work_count;
@@ -373,14 +383,26 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
         for (int p = 0; p < NP; ++p) {
             const int c0 = p * kBP;
             const int T_ = (R - c0 + kMT - 1) / kMT;  // M tiles of this panel
-            if (warp == 0 && p > 0) {
-                // producer: chunks j = 0 .. p-1 of every tile
+            // Work of the tensor cores in this panel, in order (items it = 0 .. T_):
+            //   it = 0       tile 0, chunk p - 1 only: chunks 0 .. p-2 were accumulated into
+            //                set 2 during the previous panel (its diagonal block is the
+            //                critical path of the panel, so only one chunk waits for it);
+            //   1 <= it < T_ tile it, chunks 0 .. p-1, into set it & 1;
+            //   it = T_      tile 0 of the next panel (rows c0 + 32 ..), chunks 0 .. p-1,
+            //                into set 2, once this panel's tile 0 has been read.
+            const int nch = (p > 0 ? 1 : 0) + (T_ - 1) * p + (p + 1 < NP ? p : 0);
+            if (warp == 0 && nch > 0) {
+                // producer
                 if (lane == 0) {
-                    for (int t = 0; t < T_; ++t) {
-                        const int g0 = (c0 + kMT * t) >> 3;
-                        for (int j = 0; j < p; ++j, ++cnt) {
-                            const int st = cnt % kNSt;
-                            const uint32_t rnd = cnt / kNSt;
+                    uint32_t c2 = cnt;
+                    for (int it = 0; it <= T_; ++it) {
+                        int ga = (c0 + kMT * it) >> 3, gb = c0 >> 3, j0 = 0;
+                        if (it == 0) j0 = p - 1;
+                        else if (it == T_) ga = gb = (c0 + kBP) >> 3;
+                        if (it == T_ && p + 1 >= NP) break;
+                        for (int j = max(j0, 0); j < p; ++j, ++c2) {
+                            const int st = c2 % kNSt;
+                            const uint32_t rnd = c2 / kNSt;
                             if (rnd > 0 && !vload(sh.broken) &&
                                 !umma::mbar_wait(&sh.empty[st], (rnd - 1) & 1, kPolls))
                                 vstore(sh.broken, 1);
@@ -389,26 +411,32 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                             mbar_expect_tx(&sh.full[st], P::stage);
 #pragma unroll
                             for (int s = 0; s < NSL; ++s) {
-                                bulk_g2s(dst + s * kSlA, sl + sl_off(j, s, g0, NSL, RG), kSlA, &sh.full[st]);
-                                bulk_g2s(dst + NSL * kSlA + s * kSlB, sl + sl_off(j, s, c0 >> 3, NSL, RG),
+                                bulk_g2s(dst + s * kSlA, sl + sl_off(j, s, ga, NSL, RG), kSlA, &sh.full[st]);
+                                bulk_g2s(dst + NSL * kSlA + s * kSlB, sl + sl_off(j, s, gb, NSL, RG),
                                          kSlB, &sh.full[st]);
                             }
                         }
                     }
                 }
                 __syncwarp();
-            } else if (warp == 1 && p > 0) {
+                cnt += (uint32_t)nch;
+            } else if (warp == 1 && nch > 0) {
                 // MMA issuer
                 if (lane == 0) {
                     uint32_t c2 = cnt;
-                    for (int t = 0; t < T_; ++t) {
-                        const int set = t & 1;
-                        if (use[set] > 0 && !vload(sh.broken) &&
+                    for (int it = 0; it <= T_; ++it) {
+                        if (it == T_ && p + 1 >= NP) break;
+                        const int set = (it == 0 || it == T_) ? 2 : (it & 1);
+                        const int j0 = it == 0 ? p - 1 : 0;
+                        if (j0 < 0 || j0 >= p) continue;  // nothing to multiply (panel 0)
+                        // a fresh accumulation waits until the set's last tile was read
+                        const bool fresh = it != 0 || p == 1;
+                        if (it != 0 && use[set] > 0 && !vload(sh.broken) &&
                             !umma::mbar_wait(&sh.acc_empty[set], (use[set] - 1) & 1, kPolls))
                             vstore(sh.broken, 1);
                         umma::fence_after_sync();
                         const uint32_t dacc = tmem + set * P::set_cols;
-                        for (int j = 0; j < p; ++j, ++c2) {
+                        for (int j = j0; j < p; ++j, ++c2) {
                             const int st = c2 % kNSt;
                             if (!vload(sh.broken) && !umma::mbar_wait(&sh.full[st], (c2 / kNSt) & 1, kPolls))
                                 vstore(sh.broken, 1);
@@ -416,6 +444,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                             if (!vload(sh.broken)) {
                                 const uint32_t a0 = umma::smem_addr(sm + st * P::stage);
                                 const uint32_t b0 = a0 + NSL * kSlA;
+                                const bool first = fresh && j == j0;
 #pragma unroll
                                 for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
@@ -424,20 +453,21 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                                         for (int s2 = 0; s2 < NSL - s; ++s2) {
                                             const uint64_t ad = umma::make_desc(a0 + s * kSlA + ks * 256, 128, 512);
                                             const uint64_t bd = umma::make_desc(b0 + s2 * kSlB + ks * 256, 128, 512);
-                                            umma::mma_bf16(dacc + (s + s2) * kBP, ad, bd, idesc,
-                                                           !(j == 0 && ks == 0 && s == 0));
+                                            const int lv = s + s2 < P::nlv ? s + s2 : P::nlv - 1;
+                                            umma::mma_bf16(dacc + lv * kBP, ad, bd, idesc,
+                                                           !(first && ks == 0 && s == 0 && s2 < P::nlv));
                                         }
                             }
                             umma::mma_commit(&sh.empty[st]);
                         }
-                        umma::mma_commit(&sh.acc_full[set]);
-                        ++use[set];
+                        if (it < T_) {  // the tile is complete: hand it to its epilogue group
+                            umma::mma_commit(&sh.acc_full[set]);
+                            ++use[set];
+                        }
                     }
                 }
                 __syncwarp();
-                cnt += (uint32_t)(T_ * p);
-            } else if (warp == 0 || warp == 1) {
-                // panel 0 has no earlier columns: nothing to load or multiply
+                cnt += (uint32_t)nch;
             } else if (warp >= 4) {
                 // epilogue groups: warps 4..7 take the even tiles, 8..11 the odd ones
                 const int grp = (warp - 4) >> 2, qd = warp & 3;
@@ -449,16 +479,17 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                     // P = M[r, panel] - sum_{k < c0} L[r, k] L[panel, k]
                     const int Er = valid ? (r < np ? Eg[r] : EV) : 0;
                     if (p > 0) {
-                        if (!vload(sh.broken) && !umma::mbar_wait(&sh.acc_full[grp], use[grp] & 1, kPolls))
+                        const int set = t == 0 ? 2 : (t & 1);
+                        if (!vload(sh.broken) && !umma::mbar_wait(&sh.acc_full[set], use[set] & 1, kPolls))
                             vstore(sh.broken, 1);
                         umma::fence_after_sync();
-                        const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + grp * P::set_cols;
+                        const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + set * P::set_cols;
                         // the levels hold the products' values (the slices keep their
                         // magnitudes); summed into the working type, largest level first
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
 #pragma unroll
-                            for (int l = 0; l < NSL; ++l) {
+                            for (int l = 0; l < P::nlv; ++l) {
                                 uint32_t lv[16];
                                 tmem_ld16_nowait(tb + l * kBP + 16 * h, lv);
                                 tmem_wait_ld();
@@ -472,8 +503,8 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         }
                         umma::fence_before_sync();
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(&sh.acc_empty[grp]);
-                        ++use[grp];
+                        if (lane == 0) mbar_arrive(&sh.acc_empty[set]);
+                        ++use[set];
                     } else {
 #pragma unroll
                         for (int j = 0; j < kBP; ++j) row[j] = zero<T>();
