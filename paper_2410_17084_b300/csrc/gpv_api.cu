@@ -733,11 +733,20 @@ static int gpv_solve_queue(gp_voxels_t* h, SolveCtx& x, const float* d_xyz,
         a.work_next = x.d_next + b;
         a.nmax = (B.tri_smem || tcv) ? B.hi : c.max_points;
         if (B.tall && x.d_tall && !a.pvar) {  // large voxels: the tall-matrix factorisation
+            if (tall_ss) continue;  // drained by the launch of the largest tall bucket
+            // one persistent launch drains every tall bucket, largest voxels first
+            int blo = b;
+            while (blo > 0 && P.b[blo - 1].tall) --blo;
             if (h->timing && &x == &h->main && !timed) {
                 CK(record_event(h->ev_tall[0], ss));
                 timed = true;
             }
-            CK(launch_tall(kind, a, x.d_tall, h->tall_stride, (B.hi + 31) / 32 * 32, h->sms, ss));
+            SolveArgs at = a;
+            at.work_base = x.d_bbase + blo;
+            at.work_count = x.d_bcount + blo;
+            at.work_next = x.d_next + blo;
+            at.nqueues = b - blo + 1;
+            CK(launch_tall(kind, at, x.d_tall, h->tall_stride, (B.hi + 31) / 32 * 32, h->sms, ss));
             tall_ss = ss;
         } else if (tcv) {  // the variance goes to the tensor cores
             a.percol_max = B.v.percol ? B.hi : 0;

@@ -68,6 +68,8 @@ struct SolveArgs {
     const int32_t* work_base;   // device: first entry of this launch in work[] (or null)
     const int32_t* work_count;
     int32_t* work_next;
+    int nqueues;                // the tall-matrix kernel drains queues nqueues-1 .. 0 of the
+                                // consecutive base/count/next arrays (0 or 1: one queue)
     int32_t* esc_list;
     int32_t* esc_count;
     // global-memory workspace for factors that do not fit shared memory

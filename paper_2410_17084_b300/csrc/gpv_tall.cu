@@ -69,7 +69,8 @@ constexpr int kT = 384;        // threads per CTA
 constexpr int kBP = 32;        // panel width = MMA N
 constexpr int kMT = 128;       // rows per M tile
 constexpr int kNSt = 3;        // operand stages
-constexpr uint32_t kPolls = 1u << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
+constexpr uint32_t kHintNs = 1000;            // suspend-time hint of one barrier test
 constexpr int kSlA = kMT * kBP * 2;  // bytes of one slice of a 128 x 32 A tile
 constexpr int kSlB = kBP * kBP * 2;  // bytes of one slice of a 32 x 32 B tile
 constexpr int kGrpBytes = 512;       // one 8-row group of a 32-column panel slice
@@ -101,6 +102,30 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(umma::smem_addr(mbar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase of the given parity.  Between tests the thread is suspended in the
+// barrier (up to kHintNs, or until the phase completes), so waiting warps leave the issue
+// slots to the warps that work; false after kWaitNs without completion.
+__device__ __forceinline__ bool wait_phase(uint64_t* mbar, uint32_t parity)
+{
+    const uint32_t a = umma::smem_addr(mbar);
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(a), "r"(parity), "r"(kHintNs) : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
 {
@@ -236,6 +261,18 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
     T* zp = rd + kBP;          // z of the panel
     T* Tb = zp + kBP;          // 16 x 16 products of the blocked inverse
 
+    // entries (i, m), m <= i, of the diagonal block's trailing triangles in the order
+    // e = w (w + 1) / 2 + u, w = 31 - m, u = 31 - i: the update of step k is the prefix
+    // e < (31 - k)(32 - k) / 2, so a thread keeps the entries e = ri + 128 c at every step
+    __shared__ uint16_t tri[kBP * (kBP - 1) / 2];
+    for (int e = tid; e < kBP * (kBP - 1) / 2; e += kT) {
+        int w = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while ((w + 1) * (w + 2) / 2 <= e) ++w;
+        while (w * (w + 1) / 2 > e) --w;
+        const int u = e - w * (w + 1) / 2;
+        tri[e] = (uint16_t)(((kBP - 1 - u) << 8) | (kBP - 1 - w));
+    }
+
     if (threadIdx.x < G)
         nodes[threadIdx.x] = from_d<T>(-0.5 * (double)A.size +
                                        ((double)threadIdx.x + 0.5) * (double)A.size / (double)G);
@@ -262,12 +299,18 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
     uint32_t use[3] = {0, 0, 0};    // completed tiles per accumulator set (MMA issuer, epilogue)
     const uint32_t idesc = umma::idesc_bf16(kMT, kBP);
 
-    const int total = *A.work_count;
-    const int wbase = A.work_base ? *A.work_base : 0;
+    int q = (A.nqueues > 1 ? A.nqueues : 1) - 1;  // queue being drained (largest voxels first)
     for (;;) {
         if (tid == 0) {
-            const int i = atomicAdd(A.work_next, 1);
-            sh.v = i < total ? A.work[wbase + i] : -1;
+            int vv = -1;
+            for (; q >= 0; --q) {
+                const int i = atomicAdd(A.work_next + q, 1);
+                if (i < A.work_count[q]) {
+                    vv = A.work[(A.work_base ? A.work_base[q] : 0) + i];
+                    break;
+                }
+            }
+            sh.v = vv;
             sh.abort = 0;
             sh.fail = 0;
             sh.dmin = 3.0e38f;
@@ -404,7 +447,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                             const int st = c2 % kNSt;
                             const uint32_t rnd = c2 / kNSt;
                             if (rnd > 0 && !vload(sh.broken) &&
-                                !umma::mbar_wait(&sh.empty[st], (rnd - 1) & 1, kPolls))
+                                !wait_phase(&sh.empty[st], (rnd - 1) & 1))
                                 vstore(sh.broken, 1);
                             if (vload(sh.broken)) continue;
                             unsigned char* dst = sm + st * P::stage;
@@ -432,13 +475,13 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         // a fresh accumulation waits until the set's last tile was read
                         const bool fresh = it != 0 || p == 1;
                         if (it != 0 && use[set] > 0 && !vload(sh.broken) &&
-                            !umma::mbar_wait(&sh.acc_empty[set], (use[set] - 1) & 1, kPolls))
+                            !wait_phase(&sh.acc_empty[set], (use[set] - 1) & 1))
                             vstore(sh.broken, 1);
                         umma::fence_after_sync();
                         const uint32_t dacc = tmem + set * P::set_cols;
                         for (int j = j0; j < p; ++j, ++c2) {
                             const int st = c2 % kNSt;
-                            if (!vload(sh.broken) && !umma::mbar_wait(&sh.full[st], (c2 / kNSt) & 1, kPolls))
+                            if (!vload(sh.broken) && !wait_phase(&sh.full[st], (c2 / kNSt) & 1))
                                 vstore(sh.broken, 1);
                             umma::fence_after_sync();
                             if (!vload(sh.broken)) {
@@ -480,7 +523,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                     const int Er = valid ? (r < np ? Eg[r] : EV) : 0;
                     if (p > 0) {
                         const int set = t == 0 ? 2 : (t & 1);
-                        if (!vload(sh.broken) && !umma::mbar_wait(&sh.acc_full[set], use[set] & 1, kPolls))
+                        if (!vload(sh.broken) && !wait_phase(&sh.acc_full[set], use[set] & 1))
                             vstore(sh.broken, 1);
                         umma::fence_after_sync();
                         const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + set * P::set_cols;
@@ -533,8 +576,11 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         named_sync(1, 128);
                         float dmn = 3.0e38f, dmx = 0.f;
                         int bad = 0;
-                        const int ui = ri >> 2, uq = ri & 3;  // update task: row ui, columns = uq mod 4
-                        for (int k = 0; k < kBP; ++k) {  // right-looking, one column per step
+                        // right-looking, one column and one barrier per step: step k scales
+                        // column k - 1 (its readers are past the barrier) and updates the
+                        // trailing triangle with L_ik L_mk = (A_ik / L_kk)(A_mk / L_kk)
+                        T dprev = zero<T>(), ilprev = zero<T>();
+                        for (int k = 0; k < kBP; ++k) {
                             const T d = Lkk[k * kLs + k];
                             if (ri == 0 && c0 + k < n) {
                                 const float dh = hi_of(d);
@@ -543,21 +589,26 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                                 dmx = fmaxf(dmx, dh);
                             }
                             const T il = grsqrt(d);  // 1 / L_kk
-                            if (ri > k && ri < kBP) Lkk[ri * kLs + k] = Lkk[ri * kLs + k] * il;
-                            named_sync(1, 128);
-                            if (ri == k) { Lkk[k * kLs + k] = d * il; rd[k] = il; }
-                            if (ui > k) {
-                                const T lik = Lkk[ui * kLs + k];
-                                const int m0 = k + 1 + ((uq - k - 1) & 3);
+                            if (k > 0) {
+                                if (ri >= k && ri < kBP) Lkk[ri * kLs + k - 1] = Lkk[ri * kLs + k - 1] * ilprev;
+                                else if (ri == k - 1) { Lkk[(k - 1) * kLs + k - 1] = dprev * ilprev; rd[k - 1] = ilprev; }
+                            }
+                            const int sz = kBP - 1 - k, cntk = sz * (sz + 1) / 2;
 #pragma unroll
-                                for (int s8 = 0; s8 < 8; ++s8) {
-                                    const int mm = m0 + 4 * s8;
-                                    if (mm <= ui)
-                                        Lkk[ui * kLs + mm] = gfnma(lik, Lkk[mm * kLs + k], Lkk[ui * kLs + mm]);
+                            for (int c = 0; c < 4; ++c) {
+                                const int e = ri + 128 * c;
+                                if (e < cntk) {
+                                    const int im = tri[e], i = im >> 8, m = im & 255;
+                                    const T lik = Lkk[i * kLs + k] * il, lmk = Lkk[m * kLs + k] * il;
+                                    Lkk[i * kLs + m] = gfnma(lik, lmk, Lkk[i * kLs + m]);
                                 }
                             }
+                            dprev = d;
+                            ilprev = il;
                             named_sync(1, 128);
                         }
+                        if (ri == kBP - 1) { Lkk[(kBP - 1) * kLs + kBP - 1] = dprev * ilprev; rd[kBP - 1] = ilprev; }
+                        named_sync(1, 128);
                         // D = L_pp^-1 by blocks: the eight 4 x 4 diagonal blocks directly, then
                         // three levels D21 = -D22 (L21 D11) doubling the block size; zeros above
                         for (int e = ri; e < kBP * kBP; e += 128) {
