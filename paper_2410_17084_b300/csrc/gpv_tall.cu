@@ -68,7 +68,7 @@ namespace {
 constexpr int kT = 384;        // threads per CTA
 constexpr int kBP = 32;        // panel width = MMA N
 constexpr int kMT = 128;       // rows per M tile
-constexpr int kNSt = 3;        // operand stages
+constexpr int kNSt = 3;        // most operand stages of a plan
 constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 constexpr uint32_t kHintNs = 1000;            // suspend-time hint of one barrier test
 constexpr int kSlA = kMT * kBP * 2;  // bytes of one slice of a 128 x 32 A tile
@@ -83,6 +83,10 @@ template <int NSL> struct Plan {
     static constexpr int set_cols = nlv * kBP;  // tensor-memory columns of one set
     static constexpr int tmem_cols = 512;       // three sets
     static_assert(3 * set_cols <= tmem_cols, "tensor memory");
+    // operand stages: two for float-float (measured faster than three: 1.32 against
+    // 1.36 ms per 512-point voxel and SM), three for FP32
+    static constexpr int nst = NSL == 6 ? 2 : 3;
+    static_assert(nst <= kNSt, "stages");
 };
 
 constexpr int kLs = kBP + 1;  // row stride of the diagonal-block buffers (bank spread)
@@ -91,7 +95,7 @@ constexpr int kLs = kBP + 1;  // row stride of the diagonal-block buffers (bank 
 // [T: 16 x 16, the products of the blocked inverse]
 __host__ __device__ inline int tall_smem_bytes(int nsl, int npmax, int tsize)
 {
-    int o = kNSt * nsl * (kSlA + kSlB);
+    int o = (nsl == 6 ? 2 : 3) * nsl * (kSlA + kSlB);
     o += 2 * npmax * tsize;
     o += (2 * kBP * kLs + 2 * kBP + 256) * tsize;
     return (o + 15) & ~15;
@@ -216,7 +220,9 @@ struct Sh {  // static shared state
 
 }  // namespace
 
-// Entries of K + D kept per panel: rows c0 .. np-1 of panel p, 32 values each.
+// Entries of K + D kept per panel: rows c0 .. np-1 of panel p, 32 values each, column by
+// column (entry (r, c0 + j) at j (np - c0) + r - c0), so that a warp reading one column for
+// 32 consecutive rows reads contiguous memory.
 __host__ __device__ inline int64_t tall_gram_off(int p, int np)
 {
     return (int64_t)kBP * ((int64_t)p * np - (int64_t)kBP * p * (p - 1) / 2);
@@ -253,7 +259,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
     const int G = A.G, Q = G * G;
     unsigned char* wsb = ws + (int64_t)blockIdx.x * ws_stride;
 
-    T* x1 = reinterpret_cast<T*>(sm + kNSt * P::stage);
+    T* x1 = reinterpret_cast<T*>(sm + P::nst * P::stage);
     T* x2 = x1 + npmax;
     T* Lkk = x2 + npmax;       // L of the diagonal block, 32 x 33, row-major
     T* Dm = Lkk + kBP * kLs;   // its inverse (lower triangle, zeros above)
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
             xtab[i] = ff_make(h, (float)(t - (double)h));
         }
     if (tid == 0) {
-        for (int i = 0; i < kNSt; ++i) { umma::mbar_init(&sh.full[i], 1); umma::mbar_init(&sh.empty[i], 1); }
+        for (int i = 0; i < P::nst; ++i) { umma::mbar_init(&sh.full[i], 1); umma::mbar_init(&sh.empty[i], 1); }
         for (int i = 0; i < 3; ++i) { umma::mbar_init(&sh.acc_full[i], 1); umma::mbar_init(&sh.acc_empty[i], 4); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh.broken = 0;
@@ -402,13 +408,14 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                 fb[t] = zero<T>();
             }
         }
-        // A3: K + D (lower triangle; identity on the padding), stored panel by panel so
-        // that each row's 32 entries of a panel are contiguous
+        // A3: K + D (lower triangle; identity on the padding), stored panel by panel and
+        // column by column within a panel
         for (int pp = 0; pp < NP; ++pp) {
-            const int cc0 = pp * kBP;
+            const int cc0 = pp * kBP, rows = np - cc0;
             T* gp = gram + tall_gram_off(pp, np);
-            for (int e = tid; e < (np - cc0) * kBP; e += kT) {
-                const int r = cc0 + (e >> 5), c = cc0 + (e & 31);
+            for (int e = tid; e < rows * kBP; e += kT) {
+                const int jc = e / rows;
+                const int r = cc0 + (e - jc * rows), c = cc0 + jc;
                 T o;
                 if (c > r) o = zero<T>();
                 else if (r >= n || c >= n) o = from_f<T>(r == c ? 1.f : 0.f);
@@ -444,8 +451,8 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         else if (it == T_) ga = gb = (c0 + kBP) >> 3;
                         if (it == T_ && p + 1 >= NP) break;
                         for (int j = max(j0, 0); j < p; ++j, ++c2) {
-                            const int st = c2 % kNSt;
-                            const uint32_t rnd = c2 / kNSt;
+                            const int st = c2 % P::nst;
+                            const uint32_t rnd = c2 / P::nst;
                             if (rnd > 0 && !vload(sh.broken) &&
                                 !wait_phase(&sh.empty[st], (rnd - 1) & 1))
                                 vstore(sh.broken, 1);
@@ -480,8 +487,8 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         umma::fence_after_sync();
                         const uint32_t dacc = tmem + set * P::set_cols;
                         for (int j = j0; j < p; ++j, ++c2) {
-                            const int st = c2 % kNSt;
-                            if (!vload(sh.broken) && !wait_phase(&sh.full[st], (c2 / kNSt) & 1))
+                            const int st = c2 % P::nst;
+                            if (!vload(sh.broken) && !wait_phase(&sh.full[st], (c2 / P::nst) & 1))
                                 vstore(sh.broken, 1);
                             umma::fence_after_sync();
                             if (!vload(sh.broken)) {
@@ -554,9 +561,10 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                     }
                     if (valid) {  // P = M[r, panel] - (the products of the earlier columns)
                         if (r < np) {
-                            const T* gp = gram + tall_gram_off(p, np) + (int64_t)(r - c0) * kBP;
+                            const T* gp = gram + tall_gram_off(p, np) + (r - c0);
+                            const int64_t rows = np - c0;
 #pragma unroll
-                            for (int j = 0; j < kBP; ++j) row[j] = gp[j] - row[j];
+                            for (int j = 0; j < kBP; ++j) row[j] = gp[j * rows] - row[j];
                         } else {  // cross-covariance of query q = (u, v)
                             const int q = r - np, uu = q / G, vv = q - uu * G;
 #pragma unroll
