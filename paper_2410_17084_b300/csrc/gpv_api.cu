@@ -322,13 +322,16 @@ static int tall_threshold(const gp_voxels_config* c, int Gp)
     if (c->precision == GPV_PREC_FP64 || c->tall_min_points < 0) return INT_MAX;
     int t = c->tall_min_points;
     if (t == 0) {
+        // The tall-matrix kernel solves voxels of more than about 128 points faster than
+        // the shared-memory kernels (measured on the 1M-voxel stress batch: 1.12 against
+        // 1.24 s per step in float-float; on the quadric and escalation batches too); with
+        // G > 16 its query rows lengthen every panel, so 160 there.  FP32 keeps its
+        // shared-memory kernels (and their refinement step of alpha) up to 160 points.
         const int kind = c->precision == GPV_PREC_FP32 ? PREC_F32 : PREC_FF;
-        int nsm = 0, ntcv = 0;
+        int nsm = 0;
         if (solve_max_smem_n(kind, c->grid_side, Gp, &nsm) != cudaSuccess) return INT_MAX;
-        t = nsm;
-        if (kind == PREC_FF && c->tc_workspace_mb > 0 &&
-            solve_max_smem_n(kind, c->grid_side, Gp, &ntcv, true) == cudaSuccess)
-            t = std::max(t, std::min(kTcMaxN, ntcv));
+        t = kind == PREC_F32 ? 160 : (c->grid_side > 16 ? 160 : 128);
+        t = std::min(t, nsm);
     }
     return t < c->max_points ? t : INT_MAX;
 }

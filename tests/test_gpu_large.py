@@ -101,14 +101,15 @@ def test_escalation_shapes_g32(gpv, oracle, precision):
 
 
 def test_fp32_refinement_helps(gpv, oracle):
-    """The refinement step of alpha lowers the FP32 mean error (C2 shapes)."""
+    """The refinement step of alpha lowers the FP32 mean error (C2 shapes) on the
+    shared-memory kernels (tall_min_points = -1 keeps every voxel there)."""
     from oracle import compare
     from paper_2410_17084_b300 import synth
     full = synth.quadric_batch(3000, seed=9)
     b = full.subset(np.arange(800))
     errs = {}
     for r in (0, 1):
-        out = _run(gpv, b, 0, refine=r)
+        out = _run(gpv, b, 0, refine=r, tall_min_points=-1)
         ref = compare.oracle_for_batch(b, gpu_axis=out["axis"].astype(np.int32))
         errs[r] = compare.gpr_errors(out["mean"], out["var"], ref, b.sn2, ref["status"] == 0)
     print(f"\nfp32 plain {errs[0]}\nfp32 refined {errs[1]}")

@@ -312,14 +312,14 @@ def test_autotune_keeps_parity(gpv, oracle):
 @pytest.mark.parametrize("precision", [1, 0])
 def test_factor_panel_widths(gpv, oracle, panel, precision):
     """Every panel width of the blocked shared-memory Cholesky (per-column variant off, so
-    every voxel takes it) against the oracle, on sizes across several panels and a ragged
-    last panel."""
+    every voxel takes it; tall_min_points = -1 keeps the larger voxels there too) against
+    the oracle, on sizes across several panels and a ragged last panel."""
     from paper_2410_17084_b300 import synth
     full = synth.quadric_batch(4000, seed=55)
     sel = np.nonzero((full.counts >= 20) & (full.counts <= 190))[0][:500]
     b = full.subset(np.concatenate([sel, np.argsort(full.counts)[-5:]]))
     b = b.subset(np.nonzero(b.counts <= 190)[0])
-    out = _run(gpv, b, precision, factor_panel=panel)
+    out = _run(gpv, b, precision, factor_panel=panel, tall_min_points=-1)
     tol = (MEAN_TOL, VAR_TOL) if precision else (FP32_MEAN_TOL, FP32_VAR_TOL)
     _check(gpv, b, out, oracle, *tol, f"panel {panel} prec={precision}")
 

@@ -35,7 +35,7 @@ def _run(gpv, b, init=True, **kw):
     import torch
     d = dict(voxel_size=b.size, grid_side=b.G, n_s=b.n_s, n_r=b.n_r, tau=b.tau,
              max_points=int(max(b.counts.max(), b.tau, 8)), max_voxels=max(b.nvox, 1),
-             precision=1, mean_mode=1)
+             precision=1, mean_mode=1, tall_min_points=-1)  # shared-memory kernels only
     d.update(kw)
     g = gpv.GpVoxels(gpv.gp_voxels_config_default(**d))
     dev = gpv.batch_to_device(b)
