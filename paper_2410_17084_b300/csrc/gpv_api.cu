@@ -186,11 +186,26 @@ static int validate(const gp_voxels_config* c)
 }
 
 // Bucket bounds: fixed ladder below max_points, plus the largest n whose factor fits
-// shared memory, capped at kNumBuckets buckets.
-static std::vector<int> bucket_bounds(int maxp, int nmax_smem, int extra = 0)
+// shared memory, capped at kNumBuckets buckets.  With the tall-matrix path on, its one
+// launch drains the buckets above tall_min (largest first: three bounds are enough) and
+// the ladder below it is fine, so that the smallest voxels run in CTAs sized for them.
+static std::vector<int> bucket_bounds(int maxp, int nmax_smem, int extra = 0, int tall_min = INT_MAX)
 {
-    const int ladder[] = {16, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024, 2048};
     std::vector<int> b;
+    if (tall_min < maxp) {
+        const int small[] = {8, 16, 24, 32, 48, 64, 96, 128, 160, 192};
+        for (int x : small)
+            if (x < tall_min) b.push_back(x);
+        b.push_back(tall_min);
+        for (int x : {256, 512})
+            if (x > tall_min && x < maxp) b.push_back(x);
+        b.push_back(maxp);
+        std::sort(b.begin(), b.end());
+        b.erase(std::unique(b.begin(), b.end()), b.end());
+        while ((int)b.size() > kNumBuckets) b.erase(b.begin());  // merge the smallest
+        return b;
+    }
+    const int ladder[] = {16, 32, 48, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024, 2048};
     for (int x : ladder)
         if (x < maxp) b.push_back(x);
     if (nmax_smem < maxp) b.push_back(nmax_smem);
@@ -219,7 +234,8 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         P.tc_nmax_gl = std::min(kTcMaxNGl, c.max_points);
     }
     const bool tall_on = kind == prec_kind(c.precision) && h->tall_min != INT_MAX;
-    std::vector<int> bounds = bucket_bounds(c.max_points, P.nmax_smem, P.tc_nmax);
+    std::vector<int> bounds = bucket_bounds(c.max_points, P.nmax_smem, P.tc_nmax,
+                                            tall_on ? h->tall_min : INT_MAX);
     if (tall_on && std::find(bounds.begin(), bounds.end(), h->tall_min) == bounds.end()) {
         bounds.push_back(h->tall_min);
         std::sort(bounds.begin(), bounds.end());
@@ -253,10 +269,10 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
             Bucket& B = P.b[i];
             if (B.hi > P.tc_nmax || B.tall) continue;
             B.tcv_ok = true;
-            // defaults as the autotuner picks them on the quadric workload: without the
-            // contraction, 256-thread CTAs (three per SM) beat 512 for blocked factors,
-            // 128-thread per-column ones for the small buckets
-            B.v.nthr = B.hi <= 64 ? 128 : 256;
+            // defaults as the autotuner picks them: without the contraction, 256-thread CTAs
+            // (three per SM) beat 512 for blocked factors, 128-thread per-column ones for
+            // the small buckets, one warp or two per voxel for the smallest
+            B.v.nthr = B.hi <= 16 ? 32 : (B.hi <= 32 ? 64 : (B.hi <= 64 ? 128 : 256));
             B.v.percol = c.factor_panel == 0 && B.hi <= 64;
             B.v.panel = c.factor_panel > 0 ? c.factor_panel : 4;
             B.v.smem = smem_plan(B.hi, c.grid_side, h->Gp, 8, true, B.v.nthr, true).total;
@@ -1253,7 +1269,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     int changed = 0;
-    const int cand[3] = {128, 256, 512};
+    const int cand[5] = {32, 64, 128, 256, 512};
     for (int b = 0; b < P.nb; ++b) {
         Bucket& B = P.b[b];
         if (B.tall && h->main.d_tall) continue;  // one launch shape: one CTA of 384 threads per SM
@@ -1267,9 +1283,9 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
         const int cur = best;
         const bool cur_pc = best_pc;
         const int cur_pw = best_pw;
-        for (int ci = 0; ci < 12; ++ci) {
-            const int nt = cand[ci % 3];
-            const int var = ci / 3;  // blocked with 16-, 8- or 4-column panels, or per column
+        for (int ci = 0; ci < 20; ++ci) {
+            const int nt = cand[ci % 5];
+            const int var = ci / 5;  // blocked with 16-, 8- or 4-column panels, or per column
             const bool pc = var == 3;
             const int pw = var == 0 ? 16 : (var == 1 ? 8 : 4);
             if (var > 0 && !tri) continue;  // variants of the shared-memory factor

@@ -1222,11 +1222,15 @@ cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, in
 
 // The dynamic shared-memory limit of every instantiation is raised once, when the
 // handle plans its launches (solve_occupancy), so launches stay capturable.
+// CTA sizes: 128, 256 and 512 threads; the shared-memory variants (S) also 32 and 64
+// for buckets of at most that many points (one warp or two per voxel)
 template <class T, bool S, bool V = false>
 static cudaError_t launch_t(int nthr, const SolveArgs& a, int grid, int smem, cudaStream_t s)
 {
     if (nthr == 512) k_solve<T, S, 512, V><<<grid, 512, smem, s>>>(a);
     else if (nthr == 128) k_solve<T, S, 128, V><<<grid, 128, smem, s>>>(a);
+    else if (S && nthr == 64) k_solve<T, S, S ? 64 : 256, V><<<grid, 64, smem, s>>>(a);
+    else if (S && nthr == 32) k_solve<T, S, S ? 32 : 256, V><<<grid, 32, smem, s>>>(a);
     else k_solve<T, S, 256, V><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -1262,6 +1266,8 @@ cudaError_t solve_max_smem_n(int prec, int G, int Gp, int* nmax_out, bool tcv)
 template <class T, bool S, bool V = false>
 static const void* kfun(int nthr)
 {
+    if (S && nthr == 64) return (const void*)k_solve<T, S, S ? 64 : 256, V>;
+    if (S && nthr == 32) return (const void*)k_solve<T, S, S ? 32 : 256, V>;
     return nthr == 512 ? (const void*)k_solve<T, S, 512, V>
                        : (nthr == 128 ? (const void*)k_solve<T, S, 128, V> : (const void*)k_solve<T, S, 256, V>);
 }

@@ -179,7 +179,7 @@ def test_one_per_launch_equals_batched(gpv):
     b = synth.quadric_batch(400, seed=11)
     for prec in (0, 1):
         a = _run(gpv, b, prec, tc_workspace_mb=0, tall_min_points=-1)
-        c = _run(gpv, b, prec, one_per_launch=True)
+        c = _run(gpv, b, prec, one_per_launch=True, tall_min_points=-1)  # same bucket plan
         if prec == 1:  # escalated voxels are solved in FP64 only on the batched path
             keep = (a["status"] & 2) == 0
         else:
