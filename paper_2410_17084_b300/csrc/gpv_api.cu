@@ -1270,6 +1270,57 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
     CK(cudaEventCreate(&e1));
     int changed = 0;
     const int cand[5] = {32, 64, 128, 256, 512};
+    // The shared-memory buckets of a solve run at once on their own streams, so a
+    // candidate is timed with all of them: bucket bc in the candidate's configuration,
+    // the others in their current one (each followed by its tensor-core variances).
+    auto launch_group = [&](int bc, int nt_c, bool pc_c, int pw_c, int smem_c, int grid_c,
+                            cudaEvent_t ev_start) -> int {
+        CK(cudaMemsetAsync(x.d_next, 0, sizeof(int32_t) * kNumBuckets, s));
+        if (a.tc) {  // every timed run starts from an empty workspace
+            CK(cudaMemsetAsync(reinterpret_cast<unsigned char*>(a.tc) + 8, 0, sizeof(TcCounters) - 8, s));
+            CK(cudaMemsetAsync(x.d_tc_next, 0, sizeof(int32_t) * kNumBuckets, s));
+            CK(cudaMemsetAsync(a.tc_off_v, 0xFF, sizeof(long long) * (size_t)nvox, s));
+        }
+        CK(cudaEventRecord(ev_start, s));
+        CK(cudaEventRecord(x.ev_fork, s));
+        int used = 0;
+        for (int b2 = P.nb - 1; b2 >= 0; --b2) {
+            const Bucket& B2 = P.b[b2];
+            if (B2.tall && h->main.d_tall) continue;
+            const bool tcv2 = a.tc_ws && B2.tcv_ok;
+            if (!(B2.tri_smem || tcv2)) continue;
+            const int si = (1 + b2) % kNumBuckets;
+            cudaStream_t ss = x.side[si];
+            CK(cudaStreamWaitEvent(ss, x.ev_fork, 0));
+            SolveArgs a2 = a;
+            a2.work = x.d_work;
+            a2.work_base = x.d_bbase + b2;
+            a2.work_count = x.d_bcount + b2;
+            a2.work_next = x.d_next + b2;
+            a2.nmax = B2.hi;
+            const bool mine = b2 == bc;
+            const int nt2 = mine ? nt_c : (tcv2 ? B2.v.nthr : B2.nthr);
+            const bool pc2 = mine ? pc_c : (tcv2 ? B2.v.percol : B2.percol);
+            const int pw2 = mine ? pw_c : (tcv2 ? B2.v.panel : B2.panel);
+            const int sm2 = mine ? smem_c : (tcv2 ? B2.v.smem : B2.smem);
+            const int gr2 = mine ? grid_c : (tcv2 ? B2.v.grid : B2.grid);
+            a2.percol_max = pc2 ? B2.hi : 0;
+            a2.panel = pw2;
+            CK(launch_solve(kind, true, nt2, a2, gr2, sm2, ss, tcv2));
+            if (tcv2) {
+                SolveArgs av = a2;
+                av.work_next = x.d_tc_next + b2;
+                CK(launch_var_tc(av, h->sms, ss));
+            }
+            used |= 1 << si;
+        }
+        for (int i = 0; i < kNumBuckets; ++i)
+            if (used & (1 << i)) {
+                CK(cudaEventRecord(x.ev_join[i], x.side[i]));
+                CK(cudaStreamWaitEvent(s, x.ev_join[i], 0));
+            }
+        return GPV_OK;
+    };
     for (int b = 0; b < P.nb; ++b) {
         Bucket& B = P.b[b];
         if (B.tall && h->main.d_tall) continue;  // one launch shape: one CTA of 384 threads per SM
@@ -1283,6 +1334,7 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
         const int cur = best;
         const bool cur_pc = best_pc;
         const int cur_pw = best_pw;
+        float cur_ms = 3.0e38f;
         for (int ci = 0; ci < 20; ++ci) {
             const int nt = cand[ci % 5];
             const int var = ci / 5;  // blocked with 16-, 8- or 4-column panels, or per column
@@ -1308,21 +1360,37 @@ extern "C" int gp_voxels_autotune(gp_voxels_t* h, const float* d_xyz, const int6
             float ms = 3.0e38f;
             for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel
                 CK(cudaMemsetAsync(x.d_next + b, 0, sizeof(int32_t), s));
-                if (a.tc)  // each timed launch starts from an empty workspace
+                if (a.tc) {  // each timed launch starts from an empty workspace
                     CK(cudaMemsetAsync(reinterpret_cast<unsigned char*>(a.tc) + 8, 0,
                                        sizeof(TcCounters) - 8, s));
-                CK(cudaEventRecord(e0, s));
-                CK(launch_solve(kind, tri, nt, a, grid, sp.total, s, tcv));
+                    CK(cudaMemsetAsync(x.d_tc_next + b, 0, sizeof(int32_t), s));
+                    // no voxel handed over yet: k_var_tc skips the ones this run keeps
+                    CK(cudaMemsetAsync(a.tc_off_v, 0xFF, sizeof(long long) * (size_t)nvox, s));
+                }
+                if (tri) {
+                    const int rc = launch_group(b, nt, pc, pw, sp.total, grid, e0);
+                    if (rc != GPV_OK) return rc;
+                } else {
+                    CK(cudaEventRecord(e0, s));
+                    CK(launch_solve(kind, tri, nt, a, grid, sp.total, s, tcv));
+                }
                 CK(cudaEventRecord(e1, s));
                 CK(cudaEventSynchronize(e1));
                 float t = 0.f;
                 CK(cudaEventElapsedTime(&t, e0, e1));
                 ms = std::min(ms, t);
             }
+            if (nt == cur && pc == cur_pc && pw == cur_pw) cur_ms = ms;
             if (ms < best_ms) {
                 best_ms = ms; best = nt; best_smem = sp.total; best_grid = grid; best_pc = pc;
                 best_pw = pw;
             }
+        }
+        // a change must beat the default by more than the timing noise of a lone bucket
+        if (best_ms > 0.98f * cur_ms) {
+            best = cur; best_pc = cur_pc; best_pw = cur_pw;
+            best_smem = tcv ? B.v.smem : B.smem;
+            best_grid = tcv ? B.v.grid : B.grid;
         }
         if (best != cur || best_pc != cur_pc || best_pw != cur_pw) ++changed;
         if (tcv) {
