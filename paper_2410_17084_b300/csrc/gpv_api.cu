@@ -271,8 +271,10 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
             B.tcv_ok = true;
             // defaults as the autotuner picks them: without the contraction, 256-thread CTAs
             // (three per SM) beat 512 for blocked factors, 128-thread per-column ones for
-            // the small buckets, one warp or two per voxel for the smallest
-            B.v.nthr = B.hi <= 16 ? 32 : (B.hi <= 32 ? 64 : (B.hi <= 64 ? 128 : 256));
+            // the small buckets, one warp or two per voxel for the smallest when the query
+            // grid is small (at most 128 queries, whose means the CTA forms)
+            const bool fewq = c.grid_side * c.grid_side <= 128;
+            B.v.nthr = fewq && B.hi <= 16 ? 32 : (fewq && B.hi <= 32 ? 64 : (B.hi <= 64 ? 128 : 256));
             B.v.percol = c.factor_panel == 0 && B.hi <= 64;
             B.v.panel = c.factor_panel > 0 ? c.factor_panel : 4;
             B.v.smem = smem_plan(B.hi, c.grid_side, h->Gp, 8, true, B.v.nthr, true).total;
