@@ -309,8 +309,15 @@ def make_handle(gv, batch, prec, **kw):
 
 
 def solve_leg(gv, batch, dev, prec, timed, errs=None, steps=3, warmup=2, graph=True,
-              init=True):
+              init=True, tune=True):
     g = make_handle(gv, batch, prec)
+    tuned = None
+    if tune:  # launch shapes per size bucket, on a prefix of the leg's own workload
+        pre = batch.subset(np.arange(min(batch.nvox, 100000)))
+        dp = gv.batch_to_device(pre)
+        tuned = g.autotune(dp["xyz"], dp["offsets"], dp["centres"], dp["lam"], dp["sf2"],
+                           dp["sn2"])
+        del dp
     o = g.outputs(batch.nvox, "cuda", init=init)
     f = lambda: g.solve_csr(dev["xyz"], dev["offsets"], dev["centres"], dev["lam"],
                             dev["sf2"], dev["sn2"], out=o, init=init)
@@ -323,6 +330,8 @@ def solve_leg(gv, batch, dev, prec, timed, errs=None, steps=3, warmup=2, graph=T
     res = {"value": batch.nvox / (t * 1e-3), "unit": "voxel solves/s", "ms_per_step": t,
            "steps": steps, "predicted_pts_per_s": batch.nvox * batch.G * batch.G / (t * 1e-3),
            "escalated": int(((st & gv.VOX_ESCALATED) != 0).sum())}
+    if tuned is not None:
+        res["autotune"] = f"{tuned} size buckets changed (100,000-voxel prefix)"
     if errs is not None:
         res["err"] = errs.errors(o)
     g.close()

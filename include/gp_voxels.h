@@ -439,6 +439,16 @@ GPV_API int gp_voxels_last_launches(const gp_voxels_t* h, int32_t* h_kernels);
  * Errors: GPV_EINVAL. */
 GPV_API int gp_voxels_plan_info(const gp_voxels_t* h, int32_t* h_info);
 
+/* Size buckets of this handle's launch plan, as the defaults or gp_voxels_autotune left
+ * them (a diagnostic; the paper has no counterpart).  Writes min(cap, buckets) records of
+ * five int32 each to h_info: largest n of the bucket, path (0 = shared-memory solve,
+ * 1 = global-workspace solve, 2 = tall-matrix path, 3 = shared-memory solve handing its
+ * variance to the tensor cores), CTA threads, per-column factor (0/1), panel width of the
+ * blocked factor; *h_count = number of buckets.  Host memory, owned by the caller.
+ * Errors: GPV_EINVAL (null pointers, cap < 0). */
+GPV_API int gp_voxels_bucket_info(const gp_voxels_t* h, int32_t* h_info, int32_t cap,
+                                  int32_t* h_count);
+
 /* Device time of the tall-matrix launches of this handle's batch solves (a diagnostic for
  * roofline measurement; the paper has no counterpart).  gp_voxels_set_timing(h, 1) makes
  * every later gp_voxels_solve_csr record CUDA events on the stream of those launches

@@ -253,6 +253,7 @@ static int make_plan(gp_voxels_t* h, int kind, PrecPlan& P)
         // an explicit panel width selects the blocked factor for every shared-memory bucket
         B.percol = c.factor_panel == 0 && B.tri_smem && B.hi <= default_percol_max(tsize(kind));
         B.panel = c.factor_panel > 0 ? c.factor_panel : 16;
+        if (B.tri_smem) default_bucket_shape(kind, B.hi, c.grid_side, c.factor_panel, &B.nthr, &B.panel);
         const SmemPlan sp = smem_plan(B.tri_smem ? B.hi : c.max_points, c.grid_side, h->Gp,
                                       tsize(kind), B.tri_smem, B.nthr);
         if (!B.tri_smem && (sp.pb < 4 || sp.rb < 4)) return GPV_EINVAL;  // panels too thin
@@ -1417,6 +1418,27 @@ extern "C" int gp_voxels_plan_info(const gp_voxels_t* h, int32_t* h_info)
     h_info[1] = P.tc_nmax;
     h_info[2] = P.nmax_smem;
     h_info[3] = P.nb;
+    return GPV_OK;
+}
+
+extern "C" int gp_voxels_bucket_info(const gp_voxels_t* h, int32_t* h_info, int32_t cap,
+                                     int32_t* h_count)
+{
+    if (!h || !h_info || !h_count || cap < 0) return GPV_EINVAL;
+    const PrecPlan& P = h->plan[prec_kind(h->cfg.precision)];
+    const bool tc = h->main.tc_cap > 0;
+    for (int b = 0; b < P.nb && b < cap; ++b) {
+        const Bucket& B = P.b[b];
+        const bool tall = B.tall && h->main.d_tall;
+        const bool tcv = !tall && tc && B.tcv_ok;
+        int32_t* o = h_info + 5 * b;
+        o[0] = B.hi;
+        o[1] = tall ? 2 : (tcv ? 3 : (B.tri_smem ? 0 : 1));
+        o[2] = tall ? 384 : (tcv ? B.v.nthr : B.nthr);
+        o[3] = tall ? 0 : (int)(tcv ? B.v.percol : B.percol);
+        o[4] = tall ? 32 : (tcv ? B.v.panel : B.panel);
+    }
+    *h_count = P.nb;
     return GPV_OK;
 }
 

@@ -208,6 +208,21 @@ void gpv_record_cuda_error(cudaError_t e);
 inline int solve_threads(int nmax, bool tri_in_smem) { return (!tri_in_smem || nmax >= 128) ? 512 : 256; }
 // Default per-column (rather than blocked) factor and inverse: 8-byte types up to 96 points.
 inline int default_percol_max(int tsize) { return tsize == 8 ? 96 : 0; }
+// Default CTA size and panel width of a shared-memory bucket of at most hi points.  The
+// FP32 shapes are those gp_voxels_autotune picks on the stress, quadric and escalation
+// batches: one warp per voxel up to 32 points when the grid has at most 128 queries, two
+// up to 48, 128 threads up to 64, 256 up to 160; 4-column panels for 65..96 points, 8 for
+// 97..160.  factor_panel > 0 fixes the panel width.
+inline void default_bucket_shape(int prec, int hi, int G, int factor_panel, int* nthr, int* panel)
+{
+    *nthr = solve_threads(hi, true);
+    *panel = factor_panel > 0 ? factor_panel : 16;
+    if (prec == PREC_F32 && hi <= 160) {
+        const bool fewq = G * G <= 128;
+        *nthr = fewq && hi <= 32 ? 32 : (fewq && hi <= 48 ? 64 : (hi <= 64 ? 128 : 256));
+        if (factor_panel == 0) *panel = hi <= 64 ? 16 : (hi <= 96 ? 4 : 8);
+    }
+}
 
 // Launchers (gpv_solve.cu)
 cudaError_t launch_classify(const SolveArgs& a, const int* bucket_hi, int nb, int32_t* bcount,

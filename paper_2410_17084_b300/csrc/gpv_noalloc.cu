@@ -213,7 +213,9 @@ extern "C" int gp_voxels_solve_csr_noalloc(const gp_voxels_config* c, const floa
                              scr + kOffEscCount, s)) != cudaSuccess)
         return fail(e);
     for (int b = nb - 1; b >= 0; --b) {
-        const int nt = solve_threads(bnd.hi[b], true);
+        int nt = 0, pw = 0;  // the handle path's default shape of the bucket
+        default_bucket_shape(kind, bnd.hi[b], G, c->factor_panel, &nt, &pw);
+        a.panel = pw;
         const int smem = smem_plan(bnd.hi[b], G, Gp, kind == PREC_F32 ? 4 : 8, true, nt).total;
         int occ = 0;
         if ((e = solve_occupancy(kind, true, nt, smem, &occ)) != cudaSuccess) return fail(e);

@@ -31,7 +31,8 @@ EXPORTED = [
     "gp_voxels_last_launches", "gp_voxels_autotune", "gp_voxels_solve_csr_noise",
     "gp_voxels_scan_types", "gp_voxels_type_counts", "gp_voxels_solve_alg3",
     "gp_voxels_structure_loss", "gp_voxels_render", "gp_voxels_measure_peak",
-    "gp_voxels_selftest_bounded_wait", "gp_voxels_plan_info", "gp_voxels_set_timing",
+    "gp_voxels_selftest_bounded_wait", "gp_voxels_plan_info", "gp_voxels_bucket_info",
+    "gp_voxels_set_timing",
     "gp_voxels_last_tall_ms",
 ]
 NOALLOC_MAX_VOXELS = 65536
@@ -128,6 +129,8 @@ def lib() -> ctypes.CDLL:
                                                   P, P, P]
         L.gp_voxels_last_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        L.gp_voxels_bucket_info.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32)]
         L.gp_voxels_set_timing.argtypes = [P, ctypes.c_int32]
         L.gp_voxels_last_tall_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
         L.gp_voxels_autotune.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P, P, P, P, P, P,
@@ -363,6 +366,17 @@ def gp_voxels_plan_info(h) -> dict:
     a = (ctypes.c_int32 * 4)()
     _check("gp_voxels_plan_info", lib().gp_voxels_plan_info(h, a))
     return {"tall_min": a[0], "tc_nmax": a[1], "nmax_smem": a[2], "buckets": a[3]}
+
+
+def gp_voxels_bucket_info(h) -> list:
+    """The launch plan's size buckets: dicts of hi, path, threads, percol, panel."""
+    cap = 32
+    a = (ctypes.c_int32 * (5 * cap))()
+    n = ctypes.c_int32()
+    _check("gp_voxels_bucket_info", lib().gp_voxels_bucket_info(h, a, cap, ctypes.byref(n)))
+    paths = {0: "shared", 1: "workspace", 2: "tall", 3: "shared+tc"}
+    return [{"hi": a[5 * b], "path": paths.get(a[5 * b + 1], a[5 * b + 1]), "threads": a[5 * b + 2],
+             "percol": bool(a[5 * b + 3]), "panel": a[5 * b + 4]} for b in range(min(n.value, cap))]
 
 
 def gp_voxels_set_timing(h, on: bool) -> None:
