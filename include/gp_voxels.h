@@ -58,7 +58,9 @@ enum {
     GPV_VOX_OK = 0,
     GPV_VOX_BELOW_TAU = 1,  /* n < tau: not processed (Sec. 3.1); prior written */
     GPV_VOX_ESCALATED = 2,  /* re-solved in FP64 after the conditioning check */
-    GPV_VOX_NOT_SPD = 4,    /* Gram not positive definite in the final precision */
+    GPV_VOX_NOT_SPD = 4,    /* Gram not positive definite in the final precision (in
+                               FP32 also a pivot ratio (max L_ii / min L_ii)^2 above
+                               esc_cond, which leaves no significant digit); prior written */
     GPV_VOX_TRUNCATED = 8,  /* bucket overflowed; oldest points were dropped */
     GPV_VOX_TOO_LARGE = 16, /* n > max_points: not processed; prior written */
     GPV_VOX_CONVERGED = 32, /* serving with the state machine on: the voxel had
@@ -92,7 +94,8 @@ typedef struct {
     int precision;       /* GPV_PREC_* */
     int init_mode;       /* 0: scale = sqrt(eig Phi), rotation = eigenvectors;
                             1: Eq. 8 as printed, S = diag(Phi), R = identity */
-    float esc_cond;      /* escalation threshold on (max L_ii / min L_ii)^2 */
+    float esc_cond;      /* escalation threshold on (max L_ii / min L_ii)^2 (FP32:
+                            voxels above it are reported GPV_VOX_NOT_SPD) */
     uint32_t hash_capacity; /* voxel slots of the device hash (power of two);
                             0 = no voxel store (batch solves only) */
     size_t mem_budget;   /* bytes the handle may allocate at create (0 = no limit) */

@@ -743,7 +743,10 @@ __device__ void solve_voxel(const SolveArgs& A, int v, unsigned char* smem, cons
         return;
     }
     const int64_t obase = (int64_t)v * GG;
-    if (s_fail) {
+    // FP32 without escalation: a pivot ratio beyond the threshold leaves no significant
+    // digit in the solve, so the voxel counts as not positive definite in this precision
+    const bool fail32 = sizeof(T) == 4 && !A.escalate && ill;
+    if (s_fail || fail32) {
         // not positive definite in this precision: report the prior
         for (int q = tid; q < GG; q += nthr) {
             A.mean[obase + q] = to_f(m);

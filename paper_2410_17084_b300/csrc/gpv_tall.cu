@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
             if (tid == 0 && !sh.abort) {
                 const bool ill = sh.fail || (sh.dmax > A.esc_cond * sh.dmin);
                 if (ill && A.escalate) sh.abort = 1;
-                else if (sh.fail) sh.abort = 2;
+                else if (sh.fail || (sizeof(T) == 4 && !A.escalate && ill)) sh.abort = 2;  // FP32: as above
                 if (vload(sh.broken)) sh.abort = 3;
             }
             __syncthreads();
