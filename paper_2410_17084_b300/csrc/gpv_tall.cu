@@ -584,39 +584,111 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         named_sync(1, 128);
                         float dmn = 3.0e38f, dmx = 0.f;
                         int bad = 0;
-                        // right-looking, one column and one barrier per step: step k scales
-                        // column k - 1 (its readers are past the barrier) and updates the
-                        // trailing triangle with L_ik L_mk = (A_ik / L_kk)(A_mk / L_kk)
-                        T dprev = zero<T>(), ilprev = zero<T>();
-                        for (int k = 0; k < kBP; ++k) {
-                            const T d = Lkk[k * kLs + k];
-                            if (ri == 0 && c0 + k < n) {
-                                const float dh = hi_of(d);
-                                if (!(dh > 0.f)) bad = 1;
-                                dmn = fminf(dmn, dh);
-                                dmx = fmaxf(dmx, dh);
-                            }
-                            const T il = grsqrt(d);  // 1 / L_kk
-                            if (k > 0) {
-                                if (ri >= k && ri < kBP) Lkk[ri * kLs + k - 1] = Lkk[ri * kLs + k - 1] * ilprev;
-                                else if (ri == k - 1) { Lkk[(k - 1) * kLs + k - 1] = dprev * ilprev; rd[k - 1] = ilprev; }
-                            }
-                            const int sz = kBP - 1 - k, cntk = sz * (sz + 1) / 2;
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const int e = ri + 128 * c;
-                                if (e < cntk) {
-                                    const int im = tri[e], i = im >> 8, m = im & 255;
-                                    const T lik = Lkk[i * kLs + k] * il, lmk = Lkk[m * kLs + k] * il;
-                                    Lkk[i * kLs + m] = gfnma(lik, lmk, Lkk[i * kLs + m]);
+                        // FP32 is bound by the barriers of the column steps: two columns per
+                        // step; float-float by the arithmetic's latency: one (measured: FP32
+                        // 0.52 against 0.54 ms per 512-point voxel and SM with two; float-float
+                        // 3-6% slower with two)
+                        if constexpr (sizeof(T) == 4) {
+                            // right-looking, two columns and one barrier per step: step k forms the
+                            // 2 x 2 pivot block of columns k, k+1 (every thread, redundantly), scales
+                            // columns k-2, k-1 (their readers are past the barrier) and updates the
+                            // trailing triangle by both columns, in the order and roundings of two
+                            // one-column steps: L_ik = A_ik / L_kk, L_i,k+1 = (A_i,k+1 - L_ik L_k+1,k)
+                            // / L_k+1,k+1, A_im -= L_ik L_mk, then A_im -= L_i,k+1 L_m,k+1
+                            T d0p = zero<T>(), d1p = zero<T>(), il0p = zero<T>(), il1p = zero<T>(), l10p = zero<T>();
+                            for (int k = 0; k < kBP; k += 2) {
+                                const T d0 = Lkk[k * kLs + k];
+                                const T il0 = grsqrt(d0);  // 1 / L_kk
+                                const T l10 = Lkk[(k + 1) * kLs + k] * il0;
+                                const T d1 = gfnma(l10, l10, Lkk[(k + 1) * kLs + k + 1]);
+                                const T il1 = grsqrt(d1);  // 1 / L_k+1,k+1
+                                if (ri == 0) {
+    #pragma unroll
+                                    for (int u = 0; u < 2; ++u) {
+                                        if (c0 + k + u < n) {
+                                            const float dh = hi_of(u ? d1 : d0);
+                                            if (!(dh > 0.f)) bad = 1;
+                                            dmn = fminf(dmn, dh);
+                                            dmx = fmaxf(dmx, dh);
+                                        }
+                                    }
                                 }
+                                if (k > 0) {
+                                    if (ri >= k && ri < kBP) {
+                                        const T li0 = Lkk[ri * kLs + k - 2] * il0p;
+                                        const T a1 = Lkk[ri * kLs + k - 1];
+                                        Lkk[ri * kLs + k - 2] = li0;
+                                        Lkk[ri * kLs + k - 1] = gfnma(li0, l10p, a1) * il1p;
+                                    } else if (ri == k - 2) {
+                                        Lkk[(k - 2) * kLs + k - 2] = d0p * il0p;
+                                        Lkk[(k - 1) * kLs + k - 2] = l10p;
+                                        Lkk[(k - 1) * kLs + k - 1] = d1p * il1p;
+                                        rd[k - 2] = il0p;
+                                        rd[k - 1] = il1p;
+                                    }
+                                }
+                                const int sz = kBP - 2 - k, cntk = sz * (sz + 1) / 2;  // entries, m >= k + 2
+    #pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    const int e = ri + 128 * c;
+                                    if (e < cntk) {
+                                        const int im = tri[e], i = im >> 8, m = im & 255;
+                                        const T li0 = Lkk[i * kLs + k] * il0, lm0 = Lkk[m * kLs + k] * il0;
+                                        const T li1 = gfnma(li0, l10, Lkk[i * kLs + k + 1]) * il1;
+                                        const T lm1 = gfnma(lm0, l10, Lkk[m * kLs + k + 1]) * il1;
+                                        Lkk[i * kLs + m] = gfnma(li1, lm1, gfnma(li0, lm0, Lkk[i * kLs + m]));
+                                    }
+                                }
+                                d0p = d0;
+                                d1p = d1;
+                                il0p = il0;
+                                il1p = il1;
+                                l10p = l10;
+                                named_sync(1, 128);
                             }
-                            dprev = d;
-                            ilprev = il;
+                            if (ri == kBP - 2) {  // the last pivot block
+                                Lkk[(kBP - 2) * kLs + kBP - 2] = d0p * il0p;
+                                Lkk[(kBP - 1) * kLs + kBP - 2] = l10p;
+                                Lkk[(kBP - 1) * kLs + kBP - 1] = d1p * il1p;
+                                rd[kBP - 2] = il0p;
+                                rd[kBP - 1] = il1p;
+                            }
+                            named_sync(1, 128);
+                        } else {
+                            // right-looking, one column and one barrier per step: step k scales
+                            // column k - 1 (its readers are past the barrier) and updates the
+                            // trailing triangle with L_ik L_mk = (A_ik / L_kk)(A_mk / L_kk)
+                            T dprev = zero<T>(), ilprev = zero<T>();
+                            for (int k = 0; k < kBP; ++k) {
+                                const T d = Lkk[k * kLs + k];
+                                if (ri == 0 && c0 + k < n) {
+                                    const float dh = hi_of(d);
+                                    if (!(dh > 0.f)) bad = 1;
+                                    dmn = fminf(dmn, dh);
+                                    dmx = fmaxf(dmx, dh);
+                                }
+                                const T il = grsqrt(d);  // 1 / L_kk
+                                if (k > 0) {
+                                    if (ri >= k && ri < kBP) Lkk[ri * kLs + k - 1] = Lkk[ri * kLs + k - 1] * ilprev;
+                                    else if (ri == k - 1) { Lkk[(k - 1) * kLs + k - 1] = dprev * ilprev; rd[k - 1] = ilprev; }
+                                }
+                                const int sz = kBP - 1 - k, cntk = sz * (sz + 1) / 2;
+    #pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    const int e = ri + 128 * c;
+                                    if (e < cntk) {
+                                        const int im = tri[e], i = im >> 8, m = im & 255;
+                                        const T lik = Lkk[i * kLs + k] * il, lmk = Lkk[m * kLs + k] * il;
+                                        Lkk[i * kLs + m] = gfnma(lik, lmk, Lkk[i * kLs + m]);
+                                    }
+                                }
+                                dprev = d;
+                                ilprev = il;
+                                named_sync(1, 128);
+                            }
+                            if (ri == kBP - 1) { Lkk[(kBP - 1) * kLs + kBP - 1] = dprev * ilprev; rd[kBP - 1] = ilprev; }
                             named_sync(1, 128);
                         }
-                        if (ri == kBP - 1) { Lkk[(kBP - 1) * kLs + kBP - 1] = dprev * ilprev; rd[kBP - 1] = ilprev; }
-                        named_sync(1, 128);
                         // D = L_pp^-1 by blocks: the eight 4 x 4 diagonal blocks directly, then
                         // three levels D21 = -D22 (L21 D11) doubling the block size; zeros above
                         for (int e = ri; e < kBP * kBP; e += 128) {
