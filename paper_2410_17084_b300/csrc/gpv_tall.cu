@@ -18,10 +18,11 @@
 //          P[r, :] = M[r, panel] - sum_{k < c0} L[r, k] L[panel, k]
 // a GEMM of the rows (M tiles of 128) against the panel's own rows (N = 32) over all
 // earlier columns, which the tensor cores do; then the 32 x 32 diagonal block is factored
-// (one warp, float-float), every row solves against it (L[r, panel] = P[r, :] L_pp^-T),
-// z is extended by forward substitution, and each query row adds its new entries to the
-// running sums |V_q|^2 and V_q . z.  Original entries of M are recomputed when a panel
-// needs them (kernel values from the points, K* from the separable node factors).
+// (128 threads, right-looking, one named barrier per column in float-float and per two
+// columns in FP32) and inverted by blocks, every row solves against it (L[r, panel] =
+// P[r, :] L_pp^-T as dot products with the block inverse), z is extended, and each query
+// row adds its new entries to the running sums |V_q|^2 and V_q . z.  The entries of M
+// come from K + D, formed once per voxel, and from the separable node factors of K*.
 //
 // Precision.  Each finished entry of L and V is cut into NSL slices of 8 bits on a
 // power-of-two grid fixed per row by a bound on the row's norm (Gram row r:
@@ -41,18 +42,20 @@
 // scale).  The diagonal-block factor, the solves against it and the running sums are in
 // the working type (float-float or FP32) on the CUDA cores.
 //
-// Organisation.  One persistent CTA per SM (384 threads) takes the voxels of a size
-// bucket, largest bucket first.  Warp 0 loads operand chunks (one 128 x 32 tile of each A
-// slice, one 32 x 32 tile of each B slice, contiguous in the slice store) with
-// cp.async.bulk into a ring of shared-memory stages, each completing on an mbarrier;
-// one thread of warp 1 issues the MMAs (M = 128, N = 32, K = 16, kind::f16) of a tile
-// into one of three accumulator sets (one 32-column accumulator per level) and commits:
-// tile 0 of a panel, whose diagonal block every other row waits for, has all but its last
-// chunk accumulated in set 2 during the previous panel, the other tiles alternate between
-// sets 0 and 1; warps
-// 4..7 and 8..11 take the even and odd tiles: they read the levels with tcgen05.ld (lane
-// = row), form P in the working type, solve, cut and store the slices.  Every wait is
-// bounded; a wait that gives up marks the voxel GPV_VOX_FAILED and the CTA stops.
+// Organisation.  One persistent CTA per SM (384 threads); one launch drains every size
+// bucket above the threshold, largest voxels first.  Per voxel all threads first form
+// K + D (stored per panel, column by column) and the separable K* node factors.  Warp 0
+// loads operand chunks (one 128 x 32 tile of each A slice, one 32 x 32 tile of each B
+// slice, contiguous in the slice store) with cp.async.bulk into a ring of shared-memory
+// stages (two of 60 KB in float-float, three of 40 KB in FP32), each completing on an
+// mbarrier; one thread of warp 1 issues the MMAs (M = 128, N = 32, K = 16, kind::f16) of
+// a tile into one of three accumulator sets (one 32-column accumulator per level) and
+// commits: tile 0 of a panel, whose diagonal block every other row waits for, has all but
+// its last chunk accumulated in set 2 during the previous panel, the other tiles alternate
+// between sets 0 and 1.  Warps 4..7 and 8..11 take the even and odd tiles: they read the
+// levels with tcgen05.ld (lane = row), form P in the working type, solve, cut and store
+// the slices.  Every mbarrier wait suspends in the barrier between tests and gives up
+// after 2 s; a wait that gives up marks the voxel GPV_VOX_FAILED and the CTA stops.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
