@@ -120,10 +120,14 @@ struct gp_voxels {
     int last_launches = 0;          // kernels queued by the last solve call
     // workspace of the Alg. 3 formulation (allocated by its first call)
     struct {
-        int nmax = 0, nsm = 0, kp = 0, chunk = 0;
-        float *pb = nullptr, *ps = nullptr, *fa = nullptr, *fb = nullptr, *A = nullptr;
+        int nmax = 0, nsm = 0, kp = 0, qp = 0, chunk = 0;
+        float *pk = nullptr, *tf = nullptr, *fa = nullptr, *fb = nullptr, *A = nullptr;
         uint32_t* st = nullptr;
         int32_t* n = nullptr;
+        int32_t* vidx = nullptr;    // processing order (max_voxels) and its two counters
+        int32_t* counts = nullptr;
+        cudaStream_t side = nullptr;  // the class beyond shared memory runs beside the rest
+        cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     } a3;
     // workspace of the structure similarity loss (grown on demand)
     struct LpWork {
@@ -463,8 +467,11 @@ static void release(gp_voxels_t* h)
     cudaFree(h->d_one); cudaFree(h->d_ident); cudaFree(h->d_pl_next);
     for (auto& e : h->ev_tall)
         if (e) cudaEventDestroy(e);
-    cudaFree(h->a3.pb); cudaFree(h->a3.ps); cudaFree(h->a3.fa); cudaFree(h->a3.fb); cudaFree(h->a3.A);
-    cudaFree(h->a3.st); cudaFree(h->a3.n);
+    cudaFree(h->a3.pk); cudaFree(h->a3.tf); cudaFree(h->a3.fa); cudaFree(h->a3.fb); cudaFree(h->a3.A);
+    cudaFree(h->a3.st); cudaFree(h->a3.n); cudaFree(h->a3.vidx); cudaFree(h->a3.counts);
+    if (h->a3.side) cudaStreamDestroy(h->a3.side);
+    if (h->a3.ev_fork) cudaEventDestroy(h->a3.ev_fork);
+    if (h->a3.ev_join) cudaEventDestroy(h->a3.ev_join);
     cudaFree(h->lp.keys); cudaFree(h->lp.head); cudaFree(h->lp.next); cudaFree(h->lp.pending);
     cudaFree(h->lp.counters); cudaFree(h->lp.arg); cudaFree(h->lp.best); cudaFree(h->lp.smax);
     cudaFree(h->lp.partial);
@@ -891,11 +898,11 @@ extern "C" int gp_voxels_solve_csr_noise(gp_voxels_t* h, const float* d_xyz,
                            flags, (cudaStream_t)stream, d_noise, d_pvar, nullptr);
 }
 
-// Workspace of the Alg. 3 path: k_k* (two TF32 halves) and the K* factors of `chunk`
-// voxels; the chunk is sized to about 512 MB.
+// Workspace of the Alg. 3 path: k_k* (two TF32 halves, in tensor-core operand tiles) and
+// the K* factors of `chunk` voxels; the chunk is sized to about 512 MB.
 static int alg3_workspace(gp_voxels_t* h)
 {
-    if (h->a3.pb) return GPV_OK;
+    if (h->a3.pk) return GPV_OK;
     const gp_voxels_config& c = h->cfg;
     const int G = c.grid_side, Q = G * G;
     // every voxel up to max_points: ky in shared memory up to nsm points, in a global slice
@@ -904,7 +911,9 @@ static int alg3_workspace(gp_voxels_t* h)
     const int nmax = c.max_points;
     if (nmax < c.tau) return GPV_EINVAL;
     const int kp = (nmax + 31) / 32 * 32;
-    const size_t per = (size_t)2 * Q * kp * 4 + (size_t)2 * kp * G * 4 + 8;
+    const int qp = (Q + 127) / 128 * 128;
+    const size_t tfb = (size_t)(kp / 16) * 2 * G * 20 * 4;  // K* factors per 16-point chunk
+    const size_t per = (size_t)2 * qp * kp * 4 + (size_t)2 * kp * G * 4 + tfb + 8;
     int chunk = (int)std::min<size_t>((size_t)c.max_voxels, std::max<size_t>(1, ((size_t)512 << 20) / per));
     const size_t bigA = nmax > nsm ? (size_t)alg3_big_ctas() * kp * kp * 4 : 0;
     const size_t need = per * (size_t)chunk + bigA;
@@ -917,16 +926,23 @@ static int alg3_workspace(gp_voxels_t* h)
         return GPV_OK;
     };
     int rc;
-    if ((rc = al((void**)&h->a3.pb, (size_t)chunk * Q * kp * 4)) != GPV_OK) return rc;
-    if ((rc = al((void**)&h->a3.ps, (size_t)chunk * Q * kp * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.pk, (size_t)chunk * 2 * qp * kp * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.tf, (size_t)chunk * tfb)) != GPV_OK) return rc;
     if ((rc = al((void**)&h->a3.fa, (size_t)chunk * kp * G * 4)) != GPV_OK) return rc;
     if ((rc = al((void**)&h->a3.fb, (size_t)chunk * kp * G * 4)) != GPV_OK) return rc;
     if ((rc = al((void**)&h->a3.st, (size_t)chunk * 4)) != GPV_OK) return rc;
     if ((rc = al((void**)&h->a3.n, (size_t)chunk * 4)) != GPV_OK) return rc;
     if (bigA && (rc = al((void**)&h->a3.A, bigA)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.vidx, (size_t)c.max_voxels * 4)) != GPV_OK) return rc;
+    if ((rc = al((void**)&h->a3.counts, 8)) != GPV_OK) return rc;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->a3.side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->a3.ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->a3.ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e);
     h->a3.nmax = nmax;
     h->a3.nsm = nsm;
     h->a3.kp = kp;
+    h->a3.qp = qp;
     h->a3.chunk = chunk;
     return GPV_OK;
 }
@@ -953,13 +969,21 @@ extern "C" int gp_voxels_solve_alg3(gp_voxels_t* h, const float* d_xyz, const in
     a.size = c.voxel_size; a.G = c.grid_side; a.tau = c.tau; a.mean_mode = c.mean_mode;
     a.nmax = h->a3.nmax; a.nsm = h->a3.nsm; a.kp = h->a3.kp; a.ws_A = h->a3.A;
     a.axis = d_axis; a.mean = d_mean; a.cov = d_cov; a.status = d_status;
-    a.ws_pb = h->a3.pb; a.ws_ps = h->a3.ps; a.ws_fa = h->a3.fa; a.ws_fb = h->a3.fb;
+    a.qp = h->a3.qp;
+    a.ws_pk = h->a3.pk; a.ws_tf = h->a3.tf; a.ws_fa = h->a3.fa; a.ws_fb = h->a3.fb;
     a.ws_status = h->a3.st; a.ws_n = h->a3.n;
-    h->last_launches = 0;
-    for (int32_t v0 = 0; v0 < nvox; v0 += h->a3.chunk) {
-        a.v0 = v0;
+    // voxels beyond shared memory first: they share the first chunks, where their
+    // kernel runs beside the shared-memory classes
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(h->a3.counts, 0, 8, s));
+    CK(alg3_order(d_offsets, nvox, h->a3.nsm, h->a3.nmax, c.tau, h->a3.vidx, h->a3.counts, s));
+    a.vidx = h->a3.vidx;
+    h->last_launches = 1;
+    for (int32_t s0 = 0; s0 < nvox; s0 += h->a3.chunk) {
+        a.s0 = s0;
         int nl = 0;
-        CK(alg3_launch_chunk(a, std::min(h->a3.chunk, nvox - v0), (cudaStream_t)stream, &nl));
+        CK(alg3_launch_chunk(a, std::min(h->a3.chunk, nvox - s0), s, h->a3.side, h->a3.ev_fork,
+                             h->a3.ev_join, &nl));
         h->last_launches += nl;
     }
     return GPV_OK;
