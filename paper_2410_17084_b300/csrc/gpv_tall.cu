@@ -48,11 +48,14 @@
 // loads operand chunks (one 128 x 32 tile of each A slice, one 32 x 32 tile of each B
 // slice, contiguous in the slice store) with cp.async.bulk into a ring of shared-memory
 // stages (two of 60 KB in float-float, three of 40 KB in FP32), each completing on an
-// mbarrier; one thread of warp 1 issues the MMAs (M = 128, N = 32, K = 16, kind::f16) of
-// a tile into one of three accumulator sets (one 32-column accumulator per level) and
-// commits: tile 0 of a panel, whose diagonal block every other row waits for, has all but
-// its last chunk accumulated in set 2 during the previous panel, the other tiles alternate
-// between sets 0 and 1.  Warps 4..7 and 8..11 take the even and odd tiles: they read the
+// mbarrier; one thread of warp 1 issues the MMAs (M = 128, K = 16, kind::f16) of a tile
+// into one of three accumulator sets (one 32-column accumulator per level, side by side)
+// and commits: per A slice s one MMA takes the B slices of levels s .. nlv-1 side by side
+// (N up to 160), the pairs of the shared last accumulator follow one by one (11 MMAs per
+// K step in float-float instead of 21, 4 in FP32 instead of 10: the A tile is read from
+// shared memory once per slice, not once per pair).  Tile 0 of a panel, whose diagonal
+// block every other row waits for, has all but its last chunk accumulated in set 2 during
+// the previous panel; the other tiles alternate between sets 0 and 1.  Warps 4..7 and 8..11 take the even and odd tiles: they read the
 // levels with tcgen05.ld (lane = row), form P in the working type, solve, cut and store
 // the slices.  Every mbarrier wait suspends in the barrier between tests and gives up
 // after 2 s; a wait that gives up marks the voxel GPV_VOX_FAILED and the CTA stops.
@@ -498,18 +501,28 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                                 const uint32_t a0 = umma::smem_addr(sm + st * P::stage);
                                 const uint32_t b0 = a0 + NSL * kSlA;
                                 const bool first = fresh && j == j0;
+                                // per A slice s one MMA over the B slices 0 .. nlv-1-s side by
+                                // side (N = (nlv - s) 32; they are contiguous in the stage with
+                                // the 8-row-group stride of one slice), writing the levels
+                                // s .. nlv-1, which lie side by side in tensor memory; the pairs
+                                // of the shared last accumulator (s + s2 >= nlv) one by one
 #pragma unroll
                                 for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-                                    for (int s = 0; s < NSL; ++s)
-#pragma unroll
-                                        for (int s2 = 0; s2 < NSL - s; ++s2) {
-                                            const uint64_t ad = umma::make_desc(a0 + s * kSlA + ks * 256, 128, 512);
-                                            const uint64_t bd = umma::make_desc(b0 + s2 * kSlB + ks * 256, 128, 512);
-                                            const int lv = s + s2 < P::nlv ? s + s2 : P::nlv - 1;
-                                            umma::mma_bf16(dacc + lv * kBP, ad, bd, idesc,
-                                                           !(first && ks == 0 && s == 0 && s2 < P::nlv));
+                                    for (int s = 0; s < NSL; ++s) {
+                                        const uint64_t ad = umma::make_desc(a0 + s * kSlA + ks * 256, 128, 512);
+                                        if (s < P::nlv) {
+                                            const uint64_t bd = umma::make_desc(b0 + ks * 256, 128, 512);
+                                            umma::mma_bf16(dacc + s * kBP, ad, bd,
+                                                           umma::idesc_bf16(kMT, (P::nlv - s) * kBP),
+                                                           !(first && ks == 0 && s == 0));
                                         }
+#pragma unroll
+                                        for (int s2 = (P::nlv - s > 0 ? P::nlv - s : 0); s2 < NSL - s; ++s2) {
+                                            const uint64_t bd = umma::make_desc(b0 + s2 * kSlB + ks * 256, 128, 512);
+                                            umma::mma_bf16(dacc + (P::nlv - 1) * kBP, ad, bd, idesc, true);
+                                        }
+                                    }
                             }
                             umma::mma_commit(&sh.empty[st]);
                         }
@@ -541,17 +554,23 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         // magnitudes); summed into the working type, largest level first
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
+{
+                                uint32_t lv[16];
+                                tmem_ld16_nowait(tb + 16 * h, lv);
+                                tmem_wait_ld();
 #pragma unroll
-                            for (int l = 0; l < P::nlv; ++l) {
+                                for (int jj = 0; jj < 16; ++jj) row[16 * h + jj] = from_f<T>(__uint_as_float(lv[jj]));
+                            }
+                            // the later levels in a rolled loop: the epilogue's instruction
+                            // footprint, not its operation count, bounds it (measured 4% faster
+                            // on the stress workload than the unrolled loop)
+#pragma unroll 1
+                            for (int l = 1; l < P::nlv; ++l) {
                                 uint32_t lv[16];
                                 tmem_ld16_nowait(tb + l * kBP + 16 * h, lv);
                                 tmem_wait_ld();
 #pragma unroll
-                                for (int jj = 0; jj < 16; ++jj) {
-                                    const float x = __uint_as_float(lv[jj]);
-                                    if (l == 0) row[16 * h + jj] = from_f<T>(x);
-                                    else add_f(row[16 * h + jj], x);
-                                }
+                                for (int jj = 0; jj < 16; ++jj) add_f(row[16 * h + jj], __uint_as_float(lv[jj]));
                             }
                         }
                         umma::fence_before_sync();
@@ -755,11 +774,18 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         const int g = r >> 3;
                         unsigned char* base = sl + sl_off(p, 0, g, NSL, RG) + (r & 7) * 16;
                         const int64_t sstride = (int64_t)RG * kGrpBytes;  // next slice
-                        // columns in four blocks of 8: D is lower triangular, so the dot
-                        // products of block jb stop at column 8 jb + 7
+                        // D is lower triangular: the dot products of columns j, j + 1 stop at
+                        // column j + 1.  Float-float: one rolled loop over the column pairs,
+                        // the dot products unrolled over all 32 columns and left at j + 1
+                        // (the exact triangle with the smallest instruction footprint; 12%
+                        // faster on the stress workload than blocks of 8 columns, each
+                        // unrolled to its block's end).  FP32: blocks of 8 columns, each dot
+                        // product unrolled to its block's last column (the exit test costs
+                        // more than the single FMAs it saves).
+                        constexpr int kRB = is_ff<T>::value ? kBP : 8;
 #pragma unroll
-                        for (int jb = 0; jb < kBP / 8; ++jb) {
-                            for (int j = 8 * jb; j < 8 * jb + 8; j += 2) {
+                        for (int jb = 0; jb < kBP / kRB; ++jb) {
+                            for (int j = kRB * jb; j < kRB * jb + kRB; j += 2) {
                                 T l0, l1;
                                 if (diag) {
                                     l0 = j <= lane ? Lkk[lane * kLs + j] : zero<T>();
@@ -769,7 +795,8 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                                     const T* d0 = Dm + j * kLs;
                                     const T* d1 = d0 + kLs;
 #pragma unroll
-                                    for (int k = 0; k < 8 * jb + 8; ++k) {
+                                    for (int k = 0; k < kRB * jb + kRB; ++k) {
+                                        if (is_ff<T>::value && k > j + 1) break;
                                         acc_fma(a0, row[k], d0[k]);
                                         acc_fma(a1, row[k], d1[k]);
                                     }
