@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         // magnitudes); summed into the working type, largest level first
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-{
+                            {
                                 uint32_t lv[16];
                                 tmem_ld16_nowait(tb + 16 * h, lv);
                                 tmem_wait_ld();
@@ -679,7 +679,20 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                         } else {
                             // right-looking, one column and one barrier per step: step k scales
                             // column k - 1 (its readers are past the barrier) and updates the
-                            // trailing triangle with L_ik L_mk = (A_ik / L_kk)(A_mk / L_kk)
+                            // trailing triangle with L_ik L_mk = (A_ik / L_kk)(A_mk / L_kk).  A
+                            // thread's trailing entries (e = ri + 128 c, the same at every step)
+                            // stay in registers; an entry is stored to shared memory after its
+                            // last update (step m - 1), where the next step reads it as part of
+                            // its column (measured 2.5% faster on the stress workload than
+                            // updating the entries in shared memory)
+                            int eim[4];
+                            T xr[4];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const int e = ri + 128 * c;
+                                eim[c] = e < kBP * (kBP - 1) / 2 ? (int)tri[e] : 0;
+                                xr[c] = Lkk[(eim[c] >> 8) * kLs + (eim[c] & 255)];
+                            }
                             T dprev = zero<T>(), ilprev = zero<T>();
                             for (int k = 0; k < kBP; ++k) {
                                 const T d = Lkk[k * kLs + k];
@@ -695,15 +708,18 @@ __global__ void __launch_bounds__(kT, 1) k_tall(SolveArgs A, unsigned char* ws, 
                                     else if (ri == k - 1) { Lkk[(k - 1) * kLs + k - 1] = dprev * ilprev; rd[k - 1] = ilprev; }
                                 }
                                 const int sz = kBP - 1 - k, cntk = sz * (sz + 1) / 2;
-    #pragma unroll
+                                // all four updates without branches (a select keeps the entries
+                                // already final), so their dependency chains interleave
+#pragma unroll
                                 for (int c = 0; c < 4; ++c) {
-                                    const int e = ri + 128 * c;
-                                    if (e < cntk) {
-                                        const int im = tri[e], i = im >> 8, m = im & 255;
-                                        const T lik = Lkk[i * kLs + k] * il, lmk = Lkk[m * kLs + k] * il;
-                                        Lkk[i * kLs + m] = gfnma(lik, lmk, Lkk[i * kLs + m]);
-                                    }
+                                    const int i = eim[c] >> 8, m = eim[c] & 255;
+                                    const T nx = gfnma(Lkk[i * kLs + k] * il, Lkk[m * kLs + k] * il, xr[c]);
+                                    xr[c] = ri + 128 * c < cntk ? nx : xr[c];
                                 }
+#pragma unroll
+                                for (int c = 0; c < 4; ++c)
+                                    if (ri + 128 * c < cntk && (eim[c] & 255) == k + 1)
+                                        Lkk[(eim[c] >> 8) * kLs + k + 1] = xr[c];
                                 dprev = d;
                                 ilprev = il;
                                 named_sync(1, 128);
