@@ -3,7 +3,8 @@ colour, plus depth and silhouette images) against closed forms and symmetries.
 
 Mistakes each test is meant to catch: back-to-front blending, a missing transmittance
 factor, the dilation 0.3 I left out, the quaternion read as (x, y, z, w), a transposed
-projected covariance, the early-termination rule off by one Gaussian, no near-plane cull.
+projected covariance, the early-termination rule off by one Gaussian, no near-plane cull,
+a depth key whose FP32 rounding (or wrong row of the camera rotation) misorders layers.
 """
 import math
 
@@ -90,3 +91,39 @@ def test_rotation_about_the_view_axis_transposes(oracle):
     b = _one(oracle, [0, 0, 2], [0.15, 0.03, 0.01], [c, 0, 0, s], 0.9, [1, 1, 1], W=32, H=32)[2]
     assert a[16, 21] > 0.1 and a[21, 16] < 1e-3  # elongated along x before the turn
     assert np.allclose(b, a.T, atol=1e-7)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_depth_order_is_the_exact_depth_order(oracle, seed):
+    """The order of blending is the order of the exact (FP64) camera depths, although the
+    oracle sorts and culls on a depth key rounded to FP32: twenty Gaussians on the optical
+    axis of a randomly turned and shifted camera, depths 0.01 apart (far above the key's
+    rounding), given in random order.  At the centre pixel every alpha is the opacity 0.8,
+    so T = 0.2^k after k layers and blending stops before the sixth (0.2^6 < 1e-4): the
+    depth image there is sum_k z_(k) 0.8 0.2^k over the five nearest exact depths, a value
+    that any other order of those five changes by more than 1e-4."""
+    rng = np.random.default_rng(seed)
+    Rc, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(Rc) < 0:
+        Rc[:, 0] = -Rc[:, 0]
+    tc = rng.uniform(-2, 2, 3)
+    z = 5.0 + 0.01 * rng.permutation(20)
+    t = np.stack([np.zeros(20), np.zeros(20), z], axis=1)   # camera frame, on the axis
+    P = np.float32((t - tc) @ Rc)                             # world points, rounded to FP32
+    zx = P.astype(np.float64) @ Rc[2] + tc[2]                 # their exact camera depths
+    sc = np.float32([[0.3, 0.3, 0.3]] * 20)
+    q = np.float32([[1, 0, 0, 0]] * 20)
+    op = np.float32([0.8] * 20)
+    col = np.float32([[1, 1, 1]] * 20)
+    W = H = 33
+    C, D, S, amb = oracle.rasterize(P, sc, q, op, col, Rc, tc, 40, 40, W / 2, H / 2, W, H)
+    a = float(np.float32(0.8))
+    near5 = np.sort(zx)[:5]
+    w = a * (1 - a) ** np.arange(5)
+    assert amb[16, 16] == 0
+    assert S[16, 16] == pytest.approx(w.sum(), abs=1e-9)
+    assert D[16, 16] == pytest.approx(float(near5 @ w), abs=1e-9)
+    # the same value from the shuffled inputs in another order
+    perm = rng.permutation(20)
+    _, D2, _, _ = oracle.rasterize(P[perm], sc, q, op, col, Rc, tc, 40, 40, W / 2, H / 2, W, H)
+    assert D2[16, 16] == D[16, 16]
