@@ -210,32 +210,62 @@ __global__ void k_fill(const int32_t* slot_of, const int32_t* tmap, const int32_
     seg[p] = i;
 }
 
-// one warp per visited voxel: deterministic order, ring append, marks cleared
-__global__ void k_append(const float* xyz, const int32_t* counters, const int32_t* touched,
-                         const int32_t* segsz, const int32_t* segoff, const int32_t* seg,
-                         int32_t* seg2, int nmax, float* ring, float* rnoise, float sn2,
-                         int32_t* total, int32_t* cnt, int32_t* fill, int32_t* first,
-                         int32_t* snapsz, uint32_t* vflags)
+// Ascending sort of a[0 .. c) by one warp (a in shared or global memory): Batcher's bitonic
+// network on the next power of two N >= c in the form whose comparators are all ascending
+// (the first stage of each merge of size k compares mirror images i and i ^ (k - 1), the
+// later ones i and i + j), so the positions from c up act as +infinity and their
+// comparators are skipped.  O(c log^2 c) work against O(c^2) for ranking every element.
+__device__ void warp_sort_asc(int32_t* a, int c, int lane)
 {
+    int N = 1;
+    while (N < c) N <<= 1;
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j >= 1; j >>= 1) {
+            for (int q = lane; q < (N >> 1); q += 32) {
+                const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));  // bit j of i clear
+                const int p = j == (k >> 1) ? (i ^ (k - 1)) : (i | j);
+                if (p < c) {
+                    const int32_t x = a[i], y = a[p];
+                    if (x > y) {
+                        a[i] = y;
+                        a[p] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+constexpr int kAppendWarps = 8;   // warps per k_append block (256 threads)
+constexpr int kSortCap = 1024;    // segments up to this length are sorted in shared memory
+
+// one warp per visited voxel: deterministic order, ring append, marks cleared
+__global__ void __launch_bounds__(32 * kAppendWarps)
+k_append(const float* xyz, const int32_t* counters, const int32_t* touched,
+         const int32_t* segsz, const int32_t* segoff, const int32_t* seg, int32_t* seg2,
+         int nmax, float* ring, float* rnoise, float sn2, int32_t* total, int32_t* cnt,
+         int32_t* fill, int32_t* first, int32_t* snapsz, uint32_t* vflags)
+{
+    __shared__ int32_t sbuf[kAppendWarps][kSortCap];
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= counters[0]) return;
     const int s = touched[t];
     const int c = segsz[t];
     const int base = segoff[t];
-    // rank of each new point by its index in the scan (indices are distinct)
-    for (int e = lane; e < c; e += 32) {
-        const int v = seg[base + e];
-        int r = 0;
-        for (int e2 = 0; e2 < c; ++e2) r += seg[base + e2] < v;
-        seg2[base + r] = v;
-    }
+    // the new points of the voxel in the order of their indices in the scan (a dense voxel
+    // takes a few thousand points of one scan, so ranking each point against all was the
+    // slowest part of the insert)
+    int32_t* srt = c <= kSortCap ? sbuf[threadIdx.x >> 5] : seg2 + base;
+    for (int e = lane; e < c; e += 32) srt[e] = seg[base + e];
     __syncwarp();
+    warp_sort_asc(srt, c, lane);
     const int tot = total[s];
     const int keep = c < nmax ? c : nmax;
     for (int k = c - keep + lane; k < c; k += 32) {
         const int slotpos = (int)(((int64_t)tot + k) % nmax);
-        const int src = seg2[base + k];
+        const int src = srt[k];
         float* dst = ring + ((int64_t)s * nmax + slotpos) * 3;
         dst[0] = xyz[3 * src + 0];
         dst[1] = xyz[3 * src + 1];
@@ -562,7 +592,7 @@ cudaError_t store_insert(gpv_store* st, int si, const float* d_xyz, int npts, cu
         return e;
     k_fill<<<grdp, blk, 0, s>>>(S.slot_of, st->tmap, S.segoff, npts, st->fill, S.seg, st->first,
                                 st->cnt);
-    const int wblk = 256, grdw = (V * 32 + wblk - 1) / wblk;
+    const int wblk = 32 * kAppendWarps, grdw = (V * 32 + wblk - 1) / wblk;
     k_append<<<grdw, wblk, 0, s>>>(d_xyz, S.counters, S.touched, S.segsz, S.segoff, S.seg, S.seg2,
                                    st->nmax, st->ring, st->rnoise, c->sn2, st->total, st->cnt,
                                    st->fill, st->first, S.snapsz, S.vflags);
