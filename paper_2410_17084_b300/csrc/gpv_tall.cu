@@ -41,9 +41,10 @@
 // the row's norm to about FP32's own precision).  Five slices (40 bits) kept the mean and
 // variance far inside their tolerances and were 7% faster on the stress workload, but the
 // Gaussian scales of the escalation workload's flat voxels (smallest scale near 1e-4 m)
-// then moved by 1.8e-4 relative, above the 1e-4 of the initialisation: six it is.  Pairs with s + t >= NSL are dropped (below 2^-8 NSL of the row
-// scale).  The diagonal-block factor, the solves against it and the running sums are in
-// the working type (float-float or FP32) on the CUDA cores.
+// then moved by 1.8e-4 relative, above the 1e-4 of the initialisation: six it is.  Pairs
+// with s + t >= NSL are dropped (below 2^-8 NSL of the row scale).  The diagonal-block
+// factor, the solves against it and the running sums are in the working type (float-float
+// or FP32) on the CUDA cores.
 //
 // Organisation.  One persistent CTA per SM (384 threads); one launch drains every size
 // bucket above the threshold, largest voxels first.  Per voxel all threads first form
@@ -58,10 +59,11 @@
 // K step in float-float instead of 21, 4 in FP32 instead of 10: the A tile is read from
 // shared memory once per slice, not once per pair).  Tile 0 of a panel, whose diagonal
 // block every other row waits for, has all but its last chunk accumulated in set 2 during
-// the previous panel; the other tiles alternate between sets 0 and 1.  Warps 4..7 and 8..11 take the even and odd tiles: they read the
-// levels with tcgen05.ld (lane = row), form P in the working type, solve, cut and store
-// the slices.  Every mbarrier wait suspends in the barrier between tests and gives up
-// after 2 s; a wait that gives up marks the voxel GPV_VOX_FAILED and the CTA stops.
+// the previous panel; the other tiles alternate between sets 0 and 1.  Warps 4..7 and
+// 8..11 take the even and odd tiles: they read the levels with tcgen05.ld (lane = row),
+// form P in the working type, solve, cut and store the slices.  Every mbarrier wait
+// suspends in the barrier between tests and gives up after 2 s; a wait that gives up marks
+// the voxel GPV_VOX_FAILED and the CTA stops.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
